@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Throughput of the explicit RK3 Navier-Stokes time step (Taylor-Green vortex,
+OpenSBLI paper Section 3.3) on GB300, in grid-point-stage updates per second.
+
+Workload (default): 256^3 periodic box, 4th-order central differences, FP64,
+Re 1600, M 0.1, gamma 1.4, Pr 0.71, dt = 3.385e-3 / 4 (the paper's 64^3 step
+halved per doubling), Taylor-Green initial state with seeded Gaussian noise of
+amplitude 1e-4 on each velocity component.  One bench step = one full RK3 step
+(3 stages) over the whole grid.  Variants (8th order, FP32 path) are timed on
+the same workload and reported under "variants".
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank advances its own replica (independent problems, no
+data-path collective): weak scaling, value = all ranks' point-stages / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt-stage updates/s and %HBM roofline vs plain FP64 at matched KE-decay error"
+UNIT = "grid-point-stage updates/s"
+BASE_DT_64 = 3.385e-3
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--n", type=int, default=256, help="points per axis")
+    ap.add_argument("--order", type=int, default=4)
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    n = args.n
+    return dict(workload=f"tgv_{n}^3_order{args.order}_{args.precision}", n=n, order=args.order,
+                precision=args.precision, Re=1600.0, Mach=0.1, gamma=1.4, Pr=0.71,
+                dt=BASE_DT_64 * 64.0 / n, noise_seed=1234, noise_amp=1e-4)
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work per point-stage (counted from the kernel source; FMA = 2)
+# ---------------------------------------------------------------------------
+def resid_flops_per_point(r: int) -> int:
+    d1 = 3 * r          # r subtractions + r FMAs
+    d2 = 3 * r + 1      # r additions + r FMAs + 1 multiply
+    flops = 15 * d1                # D_j Q_m
+    flops += 5 * (6 + 2) + 3 * 2   # advective/dilatation combination, mass flux
+    flops += 12 * d1 + 12          # D_j Phi_ij, D_j F_j and their sums
+    flops += 12 * d2 + 3 * 6 + 4   # Laplacians and their combination
+    flops += 5 * 4                 # RK update (2 FMAs per field)
+    return flops
+
+
+def stage_flops_per_point(r: int) -> dict:
+    prim = 1 + 3 + 5 + 2 + 2 + 9   # 1/rho, u_i, ke, p, T, momentum fluxes
+    grad = 9 * 3 * r + 2 + 15 + 3 * 7 + 3 * 3 + 2
+    return dict(prim=prim, grad=grad, resid=resid_flops_per_point(r))
+
+
+ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}  # fused minimum per point-stage
+
+
+def peaks():
+    p = dict(hbm_gbs=None, fp64_tflops=1.25, fp32_tflops=None, src="fallback")
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        p["hbm_gbs"] = m.get("hbm_gbs")
+        p["src"] = "measured"
+        p["sm_max_mhz"] = m.get("sm_max_mhz")
+    if p["hbm_gbs"] is None:
+        p["hbm_gbs"] = 6800.0
+        p["src"] = "fallback"
+    return p
+
+
+# ---------------------------------------------------------------------------
+# nvidia-smi clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def time_oracle(w, target_s=12.0, max_n=None):
+    """Times the CPU oracle on a bounded sample of the workload: one RK3 step on
+    the largest cubic grid (<= the workload's) whose step fits ~target_s."""
+    from oracle import oracle as orc
+    from paper_1609_01277_gb300 import inputs
+    orc.build()
+    n_cal = 48
+    case = orc.Case(n_cal, n_cal, n_cal, order=w["order"], Re=w["Re"], Mach=w["Mach"], dt=w["dt"])
+    Q = orc.tgv_init(case, inputs.gaussian_noise(n_cal, n_cal, n_cal, w["noise_seed"]), w["noise_amp"])
+    t0 = time.perf_counter()
+    orc.rk3_step(case, Q, 1)
+    per_pt = (time.perf_counter() - t0) / n_cal ** 3
+    n = int((target_s / per_pt) ** (1 / 3))
+    n = max(16, min(max_n or w["n"], n))
+    case = orc.Case(n, n, n, order=w["order"], Re=w["Re"], Mach=w["Mach"], dt=w["dt"])
+    Q = orc.tgv_init(case, inputs.gaussian_noise(n, n, n, w["noise_seed"]), w["noise_amp"])
+    t0 = time.perf_counter()
+    orc.rk3_step(case, Q, 1)
+    dt = time.perf_counter() - t0
+    return dict(value=3 * n ** 3 / dt, unit=UNIT, cores=orc.get_threads(), kind="oracle",
+                sample=f"1 RK3 step (3 stages) of the same Taylor-Green case on a {n}^3 grid, "
+                       f"order {w['order']}, FP64, {dt:.2f} s on {orc.get_threads()} OpenMP threads")
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, timed on bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    from paper_1609_01277_gb300 import inputs
+    w = workload(args)
+    orc.build()
+    # size each step's sample so the whole run stays within a few minutes
+    cal = time_oracle(w, target_s=2.0)
+    n = int(round((cal["value"] * 2.0 / 3.0) ** (1 / 3)))
+    n = max(16, min(w["n"], n))
+    case = orc.Case(n, n, n, order=w["order"], Re=w["Re"], Mach=w["Mach"], dt=w["dt"])
+    Q = orc.tgv_init(case, inputs.gaussian_noise(n, n, n, w["noise_seed"]), w["noise_amp"])
+    for _ in range(args.warmup):
+        Q = orc.rk3_step(case, Q, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Q = orc.rk3_step(case, Q, 1)
+    el = time.perf_counter() - t0
+    value = args.steps * 3 * n ** 3 / el
+    sample = f"each step: 1 RK3 step of the same Taylor-Green case on a {n}^3 grid (oracle, FP64)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w["workload"], "sample_grid": n, "order": w["order"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# Our CUDA path
+# ---------------------------------------------------------------------------
+def make_grid(osb, w, order, precision, noise):
+    cfg = osb.Config(w["n"], w["n"], w["n"], order=order,
+                     precision=osb.OSB_FP64 if precision == "fp64" else osb.OSB_FP32,
+                     Re=w["Re"], Mach=w["Mach"], gamma=w["gamma"], Pr=w["Pr"], dt=w["dt"])
+    g = osb.Grid(cfg)
+    g.init_taylor_green(noise, w["noise_amp"])
+    return g
+
+
+def time_steps(torch, g, steps, warmup, profile=False):
+    g.step(warmup)
+    torch.cuda.synchronize()
+    if profile:
+        g.profile_start(3 * steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.step(steps)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    prof = g.profile_stop() if profile else None
+    return e0.elapsed_time(e1), prof
+
+
+def ke_series(torch, g, steps):
+    out = [g.diagnostics()["ke"]]
+    for _ in range(steps):
+        g.step(1)
+        out.append(g.diagnostics()["ke"])
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1609_01277_gb300 import build, inputs
+    build.build()
+    from paper_1609_01277_gb300 import osb
+    osb.load()
+    w = workload(args)
+    n = w["n"]
+    npts = n ** 3
+    r = w["order"] // 2
+    noise = inputs.gaussian_noise(n, n, n, w["noise_seed"] + rank)
+    noise_dev = torch.from_numpy(noise).cuda()
+    g = make_grid(osb, w, w["order"], w["precision"], noise_dev)
+
+    clocks = Clocks(torch.cuda.current_device())
+    if world > 1:
+        dist.barrier()
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks.start()
+    ms, prof = time_steps(torch, g, args.steps, 0, profile=True)
+    clk = clocks.stop()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    units = world * args.steps * 3 * npts
+    value = units / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (the residual + update kernel)
+    pk = peaks()
+    fl = stage_flops_per_point(r)
+    res = prof["resid"]
+    avg_ms = res["total_ms"] / max(res["launches"], 1)
+    if w["precision"] == "fp64":
+        achieved = fl["resid"] * npts / (avg_ms * 1e-3) / 1e12
+        roof = {"kernel": "k_resid", "bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / pk["fp64_tflops"], "traffic": None,
+                "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s), not measured here",
+                "flops_per_point": fl["resid"]}
+    else:
+        achieved = ALG_BYTES["fp32"] * npts / (avg_ms * 1e-3) / 1e9
+        roof = {"kernel": "k_resid", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+                "peak_src": pk["src"]}
+    kernel_ms = {k: v["total_ms"] / max(v["launches"], 1) for k, v in prof.items()}
+    stage_ms = sum(kernel_ms.values())
+    roof["kernel_avg_ms"] = kernel_ms
+    roof["stage_hbm_frac"] = ALG_BYTES[w["precision"]] * npts / (stage_ms * 1e-3) / 1e9 / pk["hbm_gbs"]
+
+    # end to end through the C ABI with pinned host buffers, copies every step
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        host = torch.empty((5, n, n, n), dtype=torch.float64).pin_memory()
+        hq = host.numpy()
+        g.get_state(hq)
+        torch.cuda.synchronize()
+        ke = max(2, min(args.steps, 5))
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            g.set_state(hq)
+            g.step(1)
+            g.get_state(hq)
+        el = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([el], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            el = float(tt.item())
+        nbytes = 5 * npts * 8
+        e2e = {"value": world * ke * 3 * npts / el, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "steps": ke}
+        del host
+
+    variants = {}
+    if not args.no_variants and world == 1:
+        ref_ke = {}
+        combos = [(o, p) for o in (4, 8) for p in ("fp64", "fp32")]
+        for order, prec in combos:
+            if order == w["order"] and prec == w["precision"]:
+                vms, vprof = ms, prof
+            else:
+                gv = make_grid(osb, w, order, prec, noise_dev)
+                vms, vprof = time_steps(torch, gv, args.steps, args.warmup, profile=True)
+                del gv
+            vr = vprof["resid"]
+            vavg = vr["total_ms"] / max(vr["launches"], 1)
+            vstage = sum(v["total_ms"] / max(v["launches"], 1) for v in vprof.values())
+            ent = {"value": args.steps * 3 * npts / (vms * 1e-3), "ms_per_step": vms / args.steps,
+                   "stage_ms": vstage, "resid_ms": vavg,
+                   "stage_hbm_frac": ALG_BYTES[prec] * npts / (vstage * 1e-3) / 1e9 / pk["hbm_gbs"]}
+            if prec == "fp64":
+                ent["resid_fp64_tflops"] = stage_flops_per_point(order // 2)["resid"] * npts / (vavg * 1e-3) / 1e12
+            # KE-decay error against the FP64 run of the same order over a few steps
+            nke = min(args.steps, 10)
+            gk = make_grid(osb, w, order, prec, noise_dev)
+            series = ke_series(torch, gk, nke)
+            del gk
+            ref_ke.setdefault(order, {})[prec] = series
+            variants[f"order{order}_{prec}"] = ent
+        for order in (4, 8):
+            a, b = ref_ke[order]["fp32"], ref_ke[order]["fp64"]
+            err = max(abs(x - y) for x, y in zip(a, b)) / b[0]
+            variants[f"order{order}_fp32"]["ke_err_vs_fp64"] = err
+            variants[f"order{order}_fp32"]["speedup_vs_fp64"] = (
+                variants[f"order{order}_fp32"]["value"] / variants[f"order{order}_fp64"]["value"])
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = time_oracle(w)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "f32",
+                "data": "synthetic",
+                "config": {"workload": w["workload"], "grid": [n, n, n], "order": w["order"],
+                           "precision": w["precision"], "Re": w["Re"], "Mach": w["Mach"], "gamma": w["gamma"],
+                           "Pr": w["Pr"], "dt": w["dt"], "noise": "seeded N(0,1) x 1e-4 on u_i",
+                           "l2": f"inputs larger than L2 ({osb_bytes(w)/1e9:.1f} GB resident)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": 9 * args.steps, "variants": variants}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def osb_bytes(w):
+    n = w["n"] ** 3
+    es = 8 if w["precision"] == "fp64" else 4
+    return 10 * n * 8 + 10 * n * es + 15 * n * es
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

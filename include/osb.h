@@ -1,0 +1,171 @@
+/*
+ * osb.h -- C ABI of libosb: the explicit time step of the 3D compressible
+ * Navier-Stokes equations on a periodic structured grid, as solved for the
+ * Taylor-Green vortex in OpenSBLI (Jacobs, Jammy & Sandham, arXiv:1609.01277,
+ * Section 3.3), on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every call returns an osb_status; nothing throws across the ABI.  On an
+ *    error, osb_last_error() returns a short message for the calling thread.
+ *  - Conserved state layout: structure of arrays [field][z][y][x], x fastest,
+ *    fields (rho, rho*u0, rho*u1, rho*u2, rho*E), FP64, no padding; N = nx*ny*nz
+ *    points per field, so a host state is 5*N doubles.
+ *  - Grid: domain [0, 2*pi)^3, x_i = i*h_a with h_a = 2*pi/n_a per axis, periodic
+ *    in every direction (Section 2.2 grid, Section 2.6 periodic boundaries).
+ *  - Device memory is owned by the caller (for example allocated by PyTorch):
+ *    the library never allocates or frees device memory.  The caller passes
+ *    one state buffer and one workspace buffer per grid, sized by
+ *    osb_state_bytes() and osb_workspace_bytes(), 256-byte aligned.
+ *  - Stream: every kernel of a grid runs on the stream given at creation.
+ *    Calls that return host data synchronise that stream.  One grid must not
+ *    be used from two threads at once.
+ */
+#ifndef OSB_H
+#define OSB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    OSB_OK = 0,
+    OSB_ERR_INVALID_ARG = 1, /* bad size, order, parameter or null pointer      */
+    OSB_ERR_UNSUPPORTED = 2, /* valid request that this build does not provide */
+    OSB_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel launch failed   */
+    OSB_ERR_NONFINITE = 4,   /* the state holds NaN or Inf                      */
+    OSB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
+    OSB_ERR_BUFFER = 6       /* a buffer is too small or misaligned             */
+} osb_status;
+
+/* Arithmetic of the stencil path.  OSB_FP64: everything FP64.  OSB_FP32:
+ * stencils, products and residual in FP32 with FP32 accumulation, while the
+ * RK accumulator register and all diagnostics reductions stay FP64. */
+enum { OSB_FP64 = 0, OSB_FP32 = 1 };
+
+/* Discretisation of the viscous work d_j(u_i tau_ij) in the energy equation
+ * (Section 3.3, energy equation).  OSB_VISC_A differentiates the point-wise
+ * product u_i tau_ij (discretely conservative: total energy is kept to
+ * roundoff).  OSB_VISC_B is the product-rule expansion that the Der operator
+ * of Section 2.1.1 produces. */
+enum { OSB_VISC_A = 0, OSB_VISC_B = 1 };
+
+typedef struct {
+    int nx, ny, nz;  /* points per axis, each >= 1                            */
+    int order;       /* central-difference order 2r: 2, 4, 6, 8, 10 or 12      */
+    int precision;   /* OSB_FP64 or OSB_FP32                                   */
+    int visc_form;   /* OSB_VISC_A or OSB_VISC_B                               */
+} osb_grid_desc;
+
+/* Non-dimensional parameters (Section 3.3): Reynolds, Mach, ratio of specific
+ * heats, Prandtl number, and the time-step size.  All must be > 0, gamma > 1. */
+typedef struct {
+    double Re, Mach, gamma, Pr, dt;
+} osb_params;
+
+/* Grid means (rho_ref = 1, Omega = the whole box), Section 3.3:
+ *   ke        = <(1/2) rho u_j u_j>
+ *   enstrophy = <(1/2) rho (eps_ijk d_j u_k)^2>, d_j the first-derivative stencil
+ *   total[m]  = <Q_m> for the five conserved fields
+ *   nonfinite = number of points with a non-finite conserved value
+ *   max_cfl   = dt * max over points of sum_j (|u_j| + c)/h_j, c^2 = gamma p/rho
+ * t and step are the simulated time and the number of RK3 steps taken. */
+typedef struct {
+    double t;
+    long long step;
+    double ke, enstrophy;
+    double total[5];
+    long long nonfinite;
+    double max_cfl;
+} osb_diag;
+
+typedef struct osb_grid osb_grid; /* opaque; owns host metadata only */
+
+/* Bytes of device memory the caller must provide for the state registers of
+ * the low-storage RK3 scheme (two FP64 accumulators, two stage registers in
+ * the grid's precision).  Returns 0 for an invalid descriptor. */
+size_t osb_state_bytes(const osb_grid_desc *desc);
+
+/* Bytes of device scratch for the point-wise intermediate fields of a stage
+ * and the diagnostics partial sums.  Returns 0 for an invalid descriptor. */
+size_t osb_workspace_bytes(const osb_grid_desc *desc);
+
+/* Creates a grid over caller-owned device buffers.
+ *  state_dev / workspace_dev: device pointers, 256-byte aligned, at least
+ *    osb_state_bytes / osb_workspace_bytes long (else OSB_ERR_BUFFER).
+ *  cuda_stream: a cudaStream_t (NULL = the legacy default stream).
+ *  The state is undefined until osb_init_taylor_green or osb_set_state.
+ *  Errors: OSB_ERR_INVALID_ARG (sizes < 1, odd order, order outside 2..12,
+ *  non-positive Re, Mach, Pr, dt, or gamma <= 1), OSB_ERR_UNSUPPORTED (an order
+ *  or form without compiled kernels), OSB_ERR_BUFFER. */
+osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *params,
+                           void *state_dev, size_t state_bytes,
+                           void *workspace_dev, size_t workspace_bytes,
+                           void *cuda_stream, osb_grid **out);
+
+/* Frees the host metadata of a grid; never touches the caller's buffers. */
+osb_status osb_grid_destroy(osb_grid *grid);
+
+/* Sets the Taylor-Green initial state of Section 3.3 (L = 1):
+ *   u0 = sin x cos y cos z, u1 = -cos x sin y cos z, u2 = 0,
+ *   p  = 1/(gamma M^2) + (cos 2x + cos 2y)(2 + cos 2z)/16, T = 1 (rho = gamma M^2 p),
+ * then, if noise_dev is not NULL, u_i += noise_amp * noise_dev[i][z][y][x]
+ * at fixed rho and p.  noise_dev: device FP64, 3*N values, caller-owned (the
+ * caller draws the random numbers).  Resets t and step to 0. */
+osb_status osb_init_taylor_green(osb_grid *grid, const double *noise_dev, double noise_amp);
+
+/* Copies a conserved state (5*N FP64, layout above) from host memory in, or
+ * out to host memory.  Both synchronise the grid's stream.  set_state resets
+ * t and step to 0. */
+osb_status osb_set_state(osb_grid *grid, const double *host_src);
+osb_status osb_get_state(osb_grid *grid, double *host_dst);
+
+/* Device-to-device variants of the two calls above (stream-ordered, no sync). */
+osb_status osb_set_state_device(osb_grid *grid, const double *dev_src);
+osb_status osb_get_state_device(osb_grid *grid, double *dev_dst);
+
+/* Semi-discrete residual R(Q) = dQ/dt of the current state (no update):
+ * skew-symmetric convective terms (Section 3.3, skew-symmetric form),
+ * pressure, viscous stress with the Laplacian by the second-derivative
+ * stencil, heat flux and viscous work.  R_dev: device FP64, 5*N values,
+ * caller-owned.  In OSB_FP32 grids the residual is computed in FP32 and
+ * widened. */
+osb_status osb_residual(osb_grid *grid, double *R_dev);
+
+/* Advances the state by nsteps steps of the low-storage third-order
+ * Runge-Kutta scheme (Section 2.4): for k = 1..3,
+ *   q_k = U_{k-1} + alpha_k dt R(q_{k-1}),  U_k = U_{k-1} + beta_k dt R(q_{k-1}),
+ * alpha = (2/3, 5/12, 3/5), beta = (1/4, 3/20, 3/5), q_0 = U_0 = Q^n,
+ * Q^{n+1} = U_3.  Stream-ordered, no sync.  nsteps >= 0. */
+osb_status osb_rk3_step(osb_grid *grid, int nsteps);
+
+/* Computes the diagnostics of the current state into *out (FP64 reductions,
+ * deterministic order).  Synchronises the stream.  Returns
+ * OSB_ERR_NONFINITE (with *out filled) if any conserved value is NaN/Inf. */
+osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
+
+/* Advances n independent grids (an ensemble of uneven sizes and parameters)
+ * by nsteps steps each.  All grids must share one stream.  OSB_ERR_TIMEOUT if
+ * a bounded device-side wait gave up. */
+osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps);
+
+/* Per-kernel timing (tooling, no counterpart in the paper).  profile_start
+ * creates 4 CUDA events per stage for up to max_stages stage launches; each
+ * subsequent RK stage records them around its three kernels (primitives,
+ * gradient fluxes, residual+update) on the grid's stream.  profile_stop
+ * synchronises the stream, writes for kind k = 0, 1, 2 the summed event time
+ * total_ms[k] and launch count launches[k] (arrays of 3), and frees the
+ * events.  Stages beyond max_stages are not recorded. */
+osb_status osb_profile_start(osb_grid *grid, int max_stages);
+osb_status osb_profile_stop(osb_grid *grid, double *total_ms, long long *launches);
+
+const char *osb_status_string(osb_status status);
+const char *osb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSB_H */

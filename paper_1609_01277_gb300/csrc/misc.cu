@@ -1,0 +1,182 @@
+// misc.cu -- Taylor-Green initial state and FP64 diagnostics reductions.
+#include <math.h>
+
+#include "stage.cuh"
+
+namespace osb {
+
+// ---------------------------------------------------------------------------
+// Taylor-Green vortex initial state (OpenSBLI paper, Section 3.3), L = 1:
+//   u0 = sin x cos y cos z, u1 = -cos x sin y cos z, u2 = 0,
+//   p  = 1/(gamma M^2) + (cos 2x + cos 2y)(2 + cos 2z)/16,  T = 1 -> rho = gamma M^2 p;
+// optional u_i += amp * noise[i] at fixed rho and p.
+// ---------------------------------------------------------------------------
+__global__ void k_init_tgv(const Dims d, const Phys ph, double *__restrict__ U, size_t s,
+                           const double *__restrict__ noise, double amp) {
+    const double two_pi = 6.283185307179586476925286766559;
+    const double hx = two_pi / d.nx, hy = two_pi / d.ny, hz = two_pi / d.nz;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
+        const int x = i % d.nx, y = (i / d.nx) % d.ny, z = i / (d.nx * d.ny);
+        const double X = x * hx, Y = y * hy, Z = z * hz;
+        double sx, cx, sy, cy, sz, cz;
+        sincos(X, &sx, &cx);
+        sincos(Y, &sy, &cy);
+        sincos(Z, &sz, &cz);
+        double u0 = sx * cy * cz, u1 = -cx * sy * cz, u2 = 0.0;
+        const double p = 1.0 / ph.gM2 + (cos(2.0 * X) + cos(2.0 * Y)) * (2.0 + cos(2.0 * Z)) / 16.0;
+        const double rho = ph.gM2 * p;
+        if (noise) {
+            u0 += amp * noise[i];
+            u1 += amp * noise[d.n + i];
+            u2 += amp * noise[2 * (size_t)d.n + i];
+        }
+        U[i] = rho;
+        U[s + i] = rho * u0;
+        U[2 * s + i] = rho * u1;
+        U[3 * s + i] = rho * u2;
+        U[4 * s + i] = p / ph.gm1 + 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2);
+    }
+}
+
+cudaError_t launch_init_tgv(const Dims &d, const Phys &ph, double *U, size_t stride, const double *noise,
+                            double amp, cudaStream_t st) {
+    int blocks = (d.n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_init_tgv<<<blocks, 256, 0, st>>>(d, ph, U, stride, noise, amp);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics (Section 3.3): grid sums of (1/2) rho u_j u_j, (1/2) rho |omega|^2
+// with omega_i = eps_ijk D_j u_k, the conserved fields, the non-finite count
+// and the max of dt sum_j (|u_j| + c)/h_j.  FP64 from the FP64 accumulator.
+// Deterministic: a fixed grid-stride split, warp shuffles, a fixed-order
+// block combine, then one block combines the partials in index order.
+// ---------------------------------------------------------------------------
+constexpr int DIAG_THREADS = 256;
+constexpr int DIAG_MAX_BLOCKS = 152 * 8;
+
+int diag_num_partials(const Dims &d) {
+    int b = (d.n + DIAG_THREADS - 1) / DIAG_THREADS;
+    return b < DIAG_MAX_BLOCKS ? b : DIAG_MAX_BLOCKS;
+}
+
+__device__ __forceinline__ void diag_block_combine(double v[NDIAG], double *out) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+        for (int q = 0; q < NDIAG; ++q) {
+            const double o = __shfl_down_sync(0xffffffffu, v[q], off);
+            v[q] = (q == NDIAG - 1) ? fmax(v[q], o) : v[q] + o;
+        }
+    }
+    __shared__ double sm[DIAG_THREADS / 32][NDIAG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int q = 0; q < NDIAG; ++q) sm[warp][q] = v[q];
+    __syncthreads();
+    if (threadIdx.x < NDIAG) {
+        const int q = threadIdx.x;
+        double acc = sm[0][q];
+        for (int w = 1; w < DIAG_THREADS / 32; ++w) acc = (q == NDIAG - 1) ? fmax(acc, sm[w][q]) : acc + sm[w][q];
+        out[q] = acc;
+    }
+}
+
+template <int R>
+__device__ __forceinline__ double vel_d1(const double *__restrict__ rho, const double *__restrict__ m,
+                                         const int *off, const double *c) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = R; k >= 1; --k) {
+        const int ip = off[R + k], im = off[R - k];
+        s = fma(c[k], __ldg(m + ip) / __ldg(rho + ip) - __ldg(m + im) / __ldg(rho + im), s);
+    }
+    return s;
+}
+
+template <int R>
+__global__ void __launch_bounds__(DIAG_THREADS)
+    k_diag(const Dims d, const Phys ph, const Coef<double> c, double dt, const double *__restrict__ U,
+           size_t s, double *__restrict__ partials) {
+    double v[NDIAG];
+#pragma unroll
+    for (int q = 0; q < NDIAG; ++q) v[q] = 0.0;
+    const double two_pi = 6.283185307179586476925286766559;
+    const double ih[3] = {d.nx / two_pi, d.ny / two_pi, d.nz / two_pi};
+    const double *rho = U, *m0 = U + s, *m1 = U + 2 * s, *m2 = U + 3 * s, *e = U + 4 * s;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
+        const int x = i % d.nx, y = (i / d.nx) % d.ny, z = i / (d.nx * d.ny);
+        const double r = rho[i];
+        const double u0 = m0[i] / r, u1 = m1[i] / r, u2 = m2[i] / r;
+        const double uu = u0 * u0 + u1 * u1 + u2 * u2;
+        v[0] += 0.5 * r * uu;
+        int ox[2 * R + 1], oy[2 * R + 1], oz[2 * R + 1];
+#pragma unroll
+        for (int k = -R; k <= R; ++k) {
+            ox[k + R] = (z * d.ny + y) * d.nx + wrapc(x + k, d.nx);
+            oy[k + R] = (z * d.ny + wrapc(y + k, d.ny)) * d.nx + x;
+            oz[k + R] = (wrapc(z + k, d.nz) * d.ny + y) * d.nx + x;
+        }
+        // omega = (D_y u2 - D_z u1, D_z u0 - D_x u2, D_x u1 - D_y u0)
+        const double w0 = vel_d1<R>(rho, m2, oy, c.d1[1]) - vel_d1<R>(rho, m1, oz, c.d1[2]);
+        const double w1 = vel_d1<R>(rho, m0, oz, c.d1[2]) - vel_d1<R>(rho, m2, ox, c.d1[0]);
+        const double w2 = vel_d1<R>(rho, m1, ox, c.d1[0]) - vel_d1<R>(rho, m0, oy, c.d1[1]);
+        v[1] += 0.5 * r * (w0 * w0 + w1 * w1 + w2 * w2);
+        const double q0 = r, q1 = m0[i], q2 = m1[i], q3 = m2[i], q4 = e[i];
+        v[2] += q0;
+        v[3] += q1;
+        v[4] += q2;
+        v[5] += q3;
+        v[6] += q4;
+        const bool bad = !(isfinite(q0) && isfinite(q1) && isfinite(q2) && isfinite(q3) && isfinite(q4));
+        v[7] += bad ? 1.0 : 0.0;
+        const double p = ph.gm1 * (q4 - 0.5 * r * uu);
+        const double cs = sqrt(ph.gamma * p / r);
+        const double sum = (fabs(u0) + cs) * ih[0] + (fabs(u1) + cs) * ih[1] + (fabs(u2) + cs) * ih[2];
+        v[8] = fmax(v[8], sum * dt);
+    }
+    diag_block_combine(v, partials + (size_t)blockIdx.x * DIAG_STRIDE);
+}
+
+__global__ void __launch_bounds__(DIAG_THREADS)
+    k_diag_final(const double *__restrict__ partials, int nparts, double inv_n, double *__restrict__ result) {
+    double v[NDIAG];
+#pragma unroll
+    for (int q = 0; q < NDIAG; ++q) v[q] = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+#pragma unroll
+        for (int q = 0; q < NDIAG; ++q) {
+            const double o = partials[(size_t)b * DIAG_STRIDE + q];
+            v[q] = (q == NDIAG - 1) ? fmax(v[q], o) : v[q] + o;
+        }
+    }
+    __shared__ double out[NDIAG];
+    diag_block_combine(v, out);
+    __syncthreads();
+    if (threadIdx.x < NDIAG) {
+        const int q = threadIdx.x;
+        // means for the sums, raw count / max for the last two
+        result[q] = (q < 7) ? out[q] * inv_n : out[q];
+    }
+}
+
+cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const Coef<double> &c, double dt,
+                               const double *U, size_t stride, double *partials, int max_partials,
+                               double *result, cudaStream_t st) {
+    const int blocks = diag_num_partials(d);
+    if (blocks > max_partials) return cudaErrorInvalidValue;
+    switch (order / 2) {
+        case 1: k_diag<1><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
+        case 2: k_diag<2><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
+        case 3: k_diag<3><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
+        case 4: k_diag<4><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
+        case 5: k_diag<5><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
+        case 6: k_diag<6><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
+        default: return cudaErrorInvalidValue;
+    }
+    k_diag_final<<<1, DIAG_THREADS, 0, st>>>(partials, blocks, 1.0 / (double)d.n, result);
+    return cudaGetLastError();
+}
+
+}  // namespace osb

@@ -1,0 +1,448 @@
+// osb_api.cu -- the C ABI of libosb (declared in include/osb.h): argument
+// checks, buffer carving, the RK3 stage sequence and status codes.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "osb_internal.cuh"
+
+using namespace osb;
+
+struct osb_grid {
+    osb_grid_desc desc;
+    osb_params prm;
+    Dims d;
+    Phys ph;
+    Coef<double> c64;
+    Coef<float> c32;
+    OrderKernels K;
+    char *state;
+    char *ws;
+    cudaStream_t st;
+    int cur;  // which FP64 accumulator holds Q^n
+    double t;
+    long long step;
+    double *U[2];
+    void *q[2];
+    size_t u_stride, q_stride;
+    void *aux;
+    size_t aux_stride;
+    double *partials;
+    int max_partials;
+    double *result;
+    // profiling: 4 events per stage launch, recorded on the grid's stream
+    std::vector<cudaEvent_t> *prof_ev;
+    int prof_used, prof_cap;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+osb_status fail(osb_status s, const char *msg) {
+    g_err = msg;
+    return s;
+}
+
+osb_status cuda_fail(cudaError_t e, const char *where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return OSB_ERR_CUDA;
+}
+
+size_t round256(size_t b) { return (b + 255) / 256 * 256; }
+
+bool desc_ok(const osb_grid_desc *d) {
+    if (!d) return false;
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return false;
+    if ((long long)d->nx * d->ny * d->nz > 0x7fffffffLL) return false;
+    if (d->order < 2 || d->order > 12 || (d->order & 1)) return false;
+    if (d->precision != OSB_FP64 && d->precision != OSB_FP32) return false;
+    if (d->visc_form != OSB_VISC_A && d->visc_form != OSB_VISC_B) return false;
+    return true;
+}
+
+size_t tsize(const osb_grid_desc *d) { return d->precision == OSB_FP64 ? 8 : 4; }
+
+size_t field_bytes(size_t n, size_t es) { return round256(n * es); }
+
+size_t npoints(const osb_grid_desc *d) { return (size_t)d->nx * d->ny * d->nz; }
+
+size_t state_bytes(const osb_grid_desc *d) {
+    const size_t n = npoints(d);
+    return 2 * 5 * field_bytes(n, 8) + 2 * 5 * field_bytes(n, tsize(d));
+}
+
+size_t aux_bytes(const osb_grid_desc *d) { return NAUX * field_bytes(npoints(d), tsize(d)); }
+
+size_t diag_bytes(const osb_grid_desc *d) {
+    Dims dd{d->nx, d->ny, d->nz, (int)npoints(d)};
+    return round256((size_t)(diag_num_partials(dd) + 1) * DIAG_STRIDE * sizeof(double));
+}
+
+// Central-difference weights of order 2r (closed form): first derivative
+// c_k = (-1)^{k+1} (r!)^2 / (k (r-k)! (r+k)!), second derivative d_k = 2 c_k / k,
+// d_0 = -2 sum d_k (Section 2.4, arbitrary-order central differences).
+void fd_weights(int order, double *c, double *dd) {
+    const int r = order / 2;
+    auto fact = [](int n) {
+        double f = 1.0;
+        for (int i = 2; i <= n; ++i) f *= i;
+        return f;
+    };
+    const double rf2 = fact(r) * fact(r);
+    double s = 0.0;
+    c[0] = 0.0;
+    for (int k = 1; k <= MAXR; ++k) {
+        if (k > r) {
+            c[k] = 0.0;
+            dd[k] = 0.0;
+            continue;
+        }
+        double ck = rf2 / ((double)k * fact(r - k) * fact(r + k));
+        if (!(k & 1)) ck = -ck;
+        c[k] = ck;
+        dd[k] = 2.0 * ck / k;
+        s += dd[k];
+    }
+    dd[0] = -2.0 * s;
+}
+
+OrderKernels kernels_for(int order) {
+    switch (order) {
+        case 2: return kernels_o2();
+        case 4: return kernels_o4();
+        case 6: return kernels_o6();
+        case 8: return kernels_o8();
+        case 10: return kernels_o10();
+        case 12: return kernels_o12();
+        default: return OrderKernels{0, nullptr, nullptr};
+    }
+}
+
+StageArgs base_args(const osb_grid *g) {
+    StageArgs a;
+    memset(&a, 0, sizeof(a));
+    a.d = g->d;
+    a.ph = g->ph;
+    a.c64 = g->c64;
+    a.c32 = g->c32;
+    a.precision = g->desc.precision;
+    a.aux = g->aux;
+    a.aux_stride = g->aux_stride;
+    a.u_stride = g->u_stride;
+    a.q_stride = g->q_stride;
+    a.stream = g->st;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *osb_status_string(osb_status s) {
+    switch (s) {
+        case OSB_OK: return "ok";
+        case OSB_ERR_INVALID_ARG: return "invalid argument";
+        case OSB_ERR_UNSUPPORTED: return "unsupported";
+        case OSB_ERR_CUDA: return "CUDA error";
+        case OSB_ERR_NONFINITE: return "non-finite state";
+        case OSB_ERR_TIMEOUT: return "device wait timed out";
+        case OSB_ERR_BUFFER: return "buffer too small or misaligned";
+    }
+    return "unknown status";
+}
+
+const char *osb_last_error(void) { return g_err.c_str(); }
+
+size_t osb_state_bytes(const osb_grid_desc *d) { return desc_ok(d) ? state_bytes(d) : 0; }
+
+size_t osb_workspace_bytes(const osb_grid_desc *d) { return desc_ok(d) ? aux_bytes(d) + diag_bytes(d) : 0; }
+
+osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, void *state_dev, size_t state_len,
+                           void *ws_dev, size_t ws_len, void *stream, osb_grid **out) {
+    if (!out) return fail(OSB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc_ok(desc)) return fail(OSB_ERR_INVALID_ARG, "invalid grid descriptor");
+    if (!prm || !(prm->Re > 0) || !(prm->Mach > 0) || !(prm->Pr > 0) || !(prm->dt > 0) || !(prm->gamma > 1))
+        return fail(OSB_ERR_INVALID_ARG, "invalid physical parameters");
+    if (desc->visc_form != OSB_VISC_A) return fail(OSB_ERR_UNSUPPORTED, "viscous work form B is not built");
+    OrderKernels K = kernels_for(desc->order);
+    if (!K.stage) return fail(OSB_ERR_UNSUPPORTED, "order not instantiated");
+    if (!state_dev || !ws_dev) return fail(OSB_ERR_INVALID_ARG, "NULL device buffer");
+    if (((uintptr_t)state_dev & 255) || ((uintptr_t)ws_dev & 255))
+        return fail(OSB_ERR_BUFFER, "device buffers must be 256-byte aligned");
+    if (state_len < state_bytes(desc)) return fail(OSB_ERR_BUFFER, "state buffer too small");
+    if (ws_len < aux_bytes(desc) + diag_bytes(desc)) return fail(OSB_ERR_BUFFER, "workspace too small");
+
+    osb_grid *g = new (std::nothrow) osb_grid;
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "host allocation failed");
+    memset(g, 0, sizeof(*g));
+    g->desc = *desc;
+    g->prm = *prm;
+    const size_t n = npoints(desc);
+    g->d = Dims{desc->nx, desc->ny, desc->nz, (int)n};
+    g->ph.Re = prm->Re;
+    g->ph.Mach = prm->Mach;
+    g->ph.gamma = prm->gamma;
+    g->ph.Pr = prm->Pr;
+    g->ph.inv_re = 1.0 / prm->Re;
+    g->ph.kappa = 1.0 / ((prm->gamma - 1.0) * prm->Mach * prm->Mach * prm->Pr * prm->Re);
+    g->ph.gm1 = prm->gamma - 1.0;
+    g->ph.gM2 = prm->gamma * prm->Mach * prm->Mach;
+    double c[MAXR + 1], dd[MAXR + 1];
+    fd_weights(desc->order, c, dd);
+    const int dims[3] = {desc->nx, desc->ny, desc->nz};
+    for (int a = 0; a < 3; ++a) {
+        const double h = 2.0 * M_PI / dims[a];
+        for (int k = 0; k <= MAXR; ++k) {
+            g->c64.d1[a][k] = c[k] / h;
+            g->c64.d2[a][k] = dd[k] / (h * h);
+            g->c32.d1[a][k] = (float)g->c64.d1[a][k];
+            g->c32.d2[a][k] = (float)g->c64.d2[a][k];
+        }
+    }
+    g->K = K;
+    g->state = (char *)state_dev;
+    g->ws = (char *)ws_dev;
+    g->st = (cudaStream_t)stream;
+    const size_t es = tsize(desc);
+    const size_t f64 = field_bytes(n, 8), fT = field_bytes(n, es);
+    g->u_stride = f64 / 8;
+    g->q_stride = fT / es;
+    g->U[0] = (double *)(g->state);
+    g->U[1] = (double *)(g->state + 5 * f64);
+    g->q[0] = g->state + 10 * f64;
+    g->q[1] = g->state + 10 * f64 + 5 * fT;
+    g->aux = g->ws;
+    g->aux_stride = fT / es;
+    g->partials = (double *)(g->ws + NAUX * fT);
+    g->max_partials = diag_num_partials(g->d);
+    g->result = g->partials + (size_t)g->max_partials * DIAG_STRIDE;
+    g->cur = 0;
+    *out = g;
+    return OSB_OK;
+}
+
+static void prof_free(osb_grid *g) {
+    if (!g->prof_ev) return;
+    for (cudaEvent_t e : *g->prof_ev) cudaEventDestroy(e);
+    delete g->prof_ev;
+    g->prof_ev = nullptr;
+    g->prof_used = g->prof_cap = 0;
+}
+
+osb_status osb_grid_destroy(osb_grid *g) {
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    prof_free(g);
+    delete g;
+    return OSB_OK;
+}
+
+osb_status osb_profile_start(osb_grid *g, int max_stages) {
+    if (!g || max_stages < 1) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    prof_free(g);
+    g->prof_ev = new (std::nothrow) std::vector<cudaEvent_t>();
+    if (!g->prof_ev) return fail(OSB_ERR_INVALID_ARG, "host allocation failed");
+    g->prof_ev->resize((size_t)4 * max_stages);
+    for (auto &e : *g->prof_ev) {
+        cudaError_t err = cudaEventCreate(&e);
+        if (err != cudaSuccess) {
+            e = nullptr;
+            prof_free(g);
+            return cuda_fail(err, "profile event create");
+        }
+    }
+    g->prof_cap = max_stages;
+    g->prof_used = 0;
+    return OSB_OK;
+}
+
+osb_status osb_profile_stop(osb_grid *g, double *total_ms, long long *launches) {
+    if (!g || !total_ms || !launches) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    if (!g->prof_ev) return fail(OSB_ERR_INVALID_ARG, "profiling not started");
+    cudaError_t e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "profile sync");
+    for (int k = 0; k < KK_COUNT; ++k) {
+        total_ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (int s = 0; s < g->prof_used; ++s) {
+        cudaEvent_t *ev = g->prof_ev->data() + 4 * s;
+        for (int k = 0; k < KK_COUNT; ++k) {
+            float ms = 0.f;
+            e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            if (e != cudaSuccess) return cuda_fail(e, "profile elapsed");
+            total_ms[k] += ms;
+            launches[k] += 1;
+        }
+    }
+    prof_free(g);
+    return OSB_OK;
+}
+
+osb_status osb_init_taylor_green(osb_grid *g, const double *noise, double amp) {
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    if (noise && !isfinite(amp)) return fail(OSB_ERR_INVALID_ARG, "noise amplitude not finite");
+    cudaError_t e = launch_init_tgv(g->d, g->ph, g->U[g->cur], g->u_stride, noise, amp, g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "init_taylor_green");
+    g->t = 0.0;
+    g->step = 0;
+    return OSB_OK;
+}
+
+static osb_status copy_state(osb_grid *g, const double *src, double *dst, cudaMemcpyKind kind, bool sync) {
+    const size_t n = g->d.n;
+    for (int m = 0; m < 5; ++m) {
+        const double *s;
+        double *t;
+        if (dst == nullptr) {  // into the grid
+            s = src + m * n;
+            t = g->U[g->cur] + m * g->u_stride;
+        } else {
+            s = g->U[g->cur] + m * g->u_stride;
+            t = dst + m * n;
+        }
+        cudaError_t e = cudaMemcpyAsync(t, s, n * sizeof(double), kind, g->st);
+        if (e != cudaSuccess) return cuda_fail(e, "state copy");
+    }
+    if (sync) {
+        cudaError_t e = cudaStreamSynchronize(g->st);
+        if (e != cudaSuccess) return cuda_fail(e, "state copy sync");
+    }
+    return OSB_OK;
+}
+
+osb_status osb_set_state(osb_grid *g, const double *host_src) {
+    if (!g || !host_src) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    osb_status s = copy_state(g, host_src, nullptr, cudaMemcpyHostToDevice, true);
+    if (s == OSB_OK) {
+        g->t = 0.0;
+        g->step = 0;
+    }
+    return s;
+}
+
+osb_status osb_get_state(osb_grid *g, double *host_dst) {
+    if (!g || !host_dst) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    return copy_state(g, nullptr, host_dst, cudaMemcpyDeviceToHost, true);
+}
+
+osb_status osb_set_state_device(osb_grid *g, const double *dev_src) {
+    if (!g || !dev_src) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    osb_status s = copy_state(g, dev_src, nullptr, cudaMemcpyDeviceToDevice, false);
+    if (s == OSB_OK) {
+        g->t = 0.0;
+        g->step = 0;
+    }
+    return s;
+}
+
+osb_status osb_get_state_device(osb_grid *g, double *dev_dst) {
+    if (!g || !dev_dst) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    return copy_state(g, nullptr, dev_dst, cudaMemcpyDeviceToDevice, false);
+}
+
+osb_status osb_residual(osb_grid *g, double *R_dev) {
+    if (!g || !R_dev) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    if ((uintptr_t)R_dev & 7) return fail(OSB_ERR_BUFFER, "R_dev must be 8-byte aligned");
+    StageArgs a = base_args(g);
+    a.src = g->U[g->cur];
+    a.src_is_f64 = 1;
+    a.src_stride = g->u_stride;
+    a.R_out = R_dev;
+    a.R_stride = g->d.n;
+    cudaError_t e = g->K.residual(a);
+    if (e != cudaSuccess) return cuda_fail(e, "residual");
+    return OSB_OK;
+}
+
+// Low-storage RK3 (Section 2.4), 2-register form with alpha = (2/3, 5/12, 3/5)
+// and beta = (1/4, 3/20, 3/5).  Registers: U[cur] holds Q^n and is the stage-1
+// stencil source; U[1-cur] receives U_1..U_3 in place; q[0], q[1] hold the
+// stage values q_1, q_2 (no stage reads and writes the same stencil source).
+static const double RK_ALPHA[3] = {2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0};
+static const double RK_BETA[3] = {1.0 / 4.0, 3.0 / 20.0, 3.0 / 5.0};
+
+static osb_status rk3_one_step(osb_grid *g) {
+    StageArgs a = base_args(g);
+    double *Ucur = g->U[g->cur], *Unext = g->U[1 - g->cur];
+    const double dt = g->prm.dt;
+    for (int k = 0; k < 3; ++k) {
+        if (k == 0) {
+            a.src = Ucur;
+            a.src_is_f64 = 1;
+            a.src_stride = g->u_stride;
+            a.U_in = Ucur;
+        } else {
+            a.src = g->q[k - 1];
+            a.src_is_f64 = g->desc.precision == OSB_FP64;
+            a.src_stride = g->q_stride;
+            a.U_in = Unext;
+        }
+        a.U_out = Unext;
+        a.q_out = (k < 2) ? g->q[k] : nullptr;
+        a.alpha_dt = RK_ALPHA[k] * dt;
+        a.beta_dt = RK_BETA[k] * dt;
+        a.ev = nullptr;
+        if (g->prof_ev && g->prof_used < g->prof_cap) {
+            a.ev = g->prof_ev->data() + 4 * g->prof_used;
+            g->prof_used += 1;
+        }
+        cudaError_t e = g->K.stage(a);
+        if (e != cudaSuccess) return cuda_fail(e, "rk3 stage launch");
+    }
+    g->cur = 1 - g->cur;
+    g->step += 1;
+    g->t = g->step * dt;
+    return OSB_OK;
+}
+
+osb_status osb_rk3_step(osb_grid *g, int nsteps) {
+    if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    for (int s = 0; s < nsteps; ++s) {
+        osb_status st = rk3_one_step(g);
+        if (st != OSB_OK) return st;
+    }
+    return OSB_OK;
+}
+
+osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
+    if (!g || !out) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    cudaError_t e = launch_diagnostics(g->d, g->ph, g->desc.order, g->c64, g->prm.dt, g->U[g->cur], g->u_stride,
+                                       g->partials, g->max_partials, g->result, g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
+    double h[NDIAG];
+    e = cudaMemcpyAsync(h, g->result, sizeof(h), cudaMemcpyDeviceToHost, g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics copy");
+    e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics sync");
+    out->t = g->t;
+    out->step = g->step;
+    out->ke = h[0];
+    out->enstrophy = h[1];
+    for (int m = 0; m < 5; ++m) out->total[m] = h[2 + m];
+    out->nonfinite = (long long)h[7];
+    out->max_cfl = h[8];
+    if (out->nonfinite > 0) return fail(OSB_ERR_NONFINITE, "state holds non-finite values");
+    return OSB_OK;
+}
+
+osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) {
+    if (!grids || n < 0 || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    for (int i = 0; i < n; ++i)
+        if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
+    for (int i = 1; i < n; ++i)
+        if (grids[i]->st != grids[0]->st) return fail(OSB_ERR_INVALID_ARG, "batch grids must share one stream");
+    for (int s = 0; s < nsteps; ++s)
+        for (int i = 0; i < n; ++i) {
+            osb_status st = rk3_one_step(grids[i]);
+            if (st != OSB_OK) return st;
+        }
+    return OSB_OK;
+}
+
+}  // extern "C"

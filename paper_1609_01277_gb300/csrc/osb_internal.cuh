@@ -1,0 +1,108 @@
+// osb_internal.cuh -- internal types shared by the libosb translation units.
+//
+// Data layout in HBM (one grid):
+//   state buffer:  U0[5] U1[5]  (FP64 RK accumulators)   qA[5] qB[5] (stage
+//                  registers in the grid's precision T).  Each field starts on
+//                  a 256-byte boundary (fields padded to a multiple of 256 B).
+//   workspace:     aux[NAUX] fields of type T (point-wise intermediates of a
+//                  stage), then the diagnostics partial sums and result.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "osb.h"
+
+namespace osb {
+
+constexpr int MAXR = 6;  // orders 2..12
+
+// Point-wise intermediate fields written by the primitive and gradient
+// kernels of a stage and read by the residual kernel.
+enum Aux {
+    A_U = 0, A_V, A_W,        // velocity u_i = (rho u_i)/rho
+    A_P, A_T,                 // pressure, temperature
+    A_PXX, A_PYY, A_PZZ,      // momentum flux Phi_ii = rho u_i u_i/2 + p - g_i/(3 Re)
+    A_PXY, A_PXZ, A_PYZ,      // momentum flux Phi_ij = rho u_i u_j/2 (i != j)
+    A_FX, A_FY, A_FZ,         // energy flux F_j = (rho E/2 + p) u_j - u_i tau_ij
+    A_DIV,                    // d_k u_k
+    NAUX
+};
+
+constexpr int NDIAG = 9;        // ke, enstrophy, totals[5], nonfinite, max_cfl
+constexpr int DIAG_STRIDE = 16; // doubles per partial record
+
+template <typename T>
+__host__ __device__ inline size_t padded(size_t n) {
+    size_t per = 256 / sizeof(T);
+    return (n + per - 1) / per * per;
+}
+
+struct Dims {
+    int nx, ny, nz;
+    int n;  // nx*ny*nz (< 2^31)
+};
+
+struct Phys {
+    double Re, Mach, gamma, Pr;
+    double inv_re, kappa, gm1, gM2;
+};
+
+// Stencil weights pre-divided by the grid spacing: d1[a][k] = c_k / h_a
+// (k = 1..r), d2[a][k] = d_k / h_a^2 (k = 0..r).
+template <typename T>
+struct Coef {
+    T d1[3][MAXR + 1];
+    T d2[3][MAXR + 1];
+};
+
+// Everything a stage launch needs.
+struct StageArgs {
+    Dims d;
+    Phys ph;
+    Coef<double> c64;
+    Coef<float> c32;
+    int precision;          // OSB_FP64 / OSB_FP32
+    const void *src;        // stencil source q_{k-1}
+    int src_is_f64;         // 1: src holds doubles (U register), 0: type T
+    size_t src_stride;      // elements between fields of src
+    void *aux;              // NAUX fields of type T
+    size_t aux_stride;
+    const double *U_in;     // RK accumulator read at the point
+    double *U_out;          // RK accumulator written at the point (may equal U_in)
+    void *q_out;            // next stage register (type T), or nullptr
+    size_t u_stride, q_stride;
+    double alpha_dt, beta_dt;
+    double *R_out;          // residual-only mode: FP64 residual (5 fields, R_stride)
+    size_t R_stride;
+    cudaStream_t stream;
+    cudaEvent_t *ev;        // optional: 4 events recorded around the 3 kernels
+};
+
+// Kernel kinds reported by the profiling hooks.
+enum KernelKind { KK_PRIM = 0, KK_GRAD = 1, KK_RESID = 2, KK_COUNT = 3 };
+
+struct OrderKernels {
+    int order;
+    cudaError_t (*stage)(const StageArgs &);     // prim + grad + residual/update
+    cudaError_t (*residual)(const StageArgs &);  // prim + grad + residual only
+};
+
+// One translation unit per order provides its launcher table.
+OrderKernels kernels_o2();
+OrderKernels kernels_o4();
+OrderKernels kernels_o6();
+OrderKernels kernels_o8();
+OrderKernels kernels_o10();
+OrderKernels kernels_o12();
+
+// Misc kernels (init, diagnostics).
+cudaError_t launch_init_tgv(const Dims &d, const Phys &ph, double *U, size_t stride,
+                            const double *noise, double amp, cudaStream_t st);
+cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const Coef<double> &c,
+                               double dt, const double *U, size_t stride, double *partials,
+                               int max_partials, double *result, cudaStream_t st);
+int diag_num_partials(const Dims &d);
+
+}  // namespace osb

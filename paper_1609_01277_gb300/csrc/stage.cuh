@@ -1,0 +1,276 @@
+// stage.cuh -- one stage of the low-storage RK3 step for the compressible
+// Navier-Stokes equations (OpenSBLI paper, Section 3.3), templated on the
+// stencil radius R (order 2R), the stencil source type S and the arithmetic
+// type T.  Included once per order by stage_o<2R>.cu.
+//
+// A stage is three kernels, each visiting every point once:
+//   k_prim : point-wise primitives and momentum fluxes           (reads Q)
+//   k_grad : velocity gradient -> tau, energy flux, div u       (stencils on u)
+//   k_resid: all remaining derivatives, the residual R and the RK update
+// Each FP64 operation of the residual is executed once per point: on GB300
+// FP64 issues at 1/64 of the FP32 rate, so re-computing intermediates in
+// stencil halos costs more than writing and re-reading them (HBM and L2 have
+// ample headroom at FP64 arithmetic rates).
+//
+// Residual, with Q = (rho, m_i = rho u_i, e = rho E), D_j / L_j the first /
+// second-derivative stencils along j, g_i = div u - D_i u_i:
+//   R_rho = -sum_j D_j(m_j/2)     - A(rho)
+//   R_mi  = -sum_j D_j Phi_ij     - A(m_i) + (1/Re)[sum_j L_j u_i + L_i u_i/3]
+//   R_e   = -sum_j D_j F_j        - A(e)   + kappa sum_j L_j T
+//   A(a)  = (sum_j u_j D_j a + a div u)/2
+//   Phi_ij = m_i u_j/2 + delta_ij (p - g_i/(3 Re)),
+//   F_j    = (e/2 + p) u_j - u_i tau_ij.
+// This is the skew-symmetric convective form, the pressure terms, d_j tau_ij
+// (Laplacian by L, mixed terms as D_i(D_k u_k)) and the conservative viscous
+// work and heat flux, regrouped by linearity of D_j.
+#pragma once
+
+#include "osb_internal.cuh"
+
+namespace osb {
+
+template <typename T>
+struct CoefPick;
+template <>
+struct CoefPick<double> {
+    static __device__ __forceinline__ const Coef<double> &get(const StageArgs &a) { return a.c64; }
+};
+template <>
+struct CoefPick<float> {
+    static __device__ __forceinline__ const Coef<float> &get(const StageArgs &a) { return a.c32; }
+};
+
+__device__ __forceinline__ int wrapc(int i, int n) {
+    i %= n;
+    return i < 0 ? i + n : i;
+}
+
+// Wrapped neighbour offsets of one point, per axis, k = -R..R.
+template <int R>
+struct Nbr {
+    int x[2 * R + 1];  // wrapped x + k
+    int y[2 * R + 1];  // wrapped (y + k) * nx
+    int z[2 * R + 1];  // wrapped (z + k) * nx * ny
+    __device__ __forceinline__ void init(int px, int py, int pz, const Dims &d) {
+#pragma unroll
+        for (int k = -R; k <= R; ++k) {
+            x[k + R] = wrapc(px + k, d.nx);
+            y[k + R] = wrapc(py + k, d.ny) * d.nx;
+            z[k + R] = wrapc(pz + k, d.nz) * d.nx * d.ny;
+        }
+    }
+    template <int AX>
+    __device__ __forceinline__ int at(int k) const {
+        if (AX == 0) return z[R] + y[R] + x[R + k];
+        if (AX == 1) return z[R] + y[R + k] + x[R];
+        return z[R + k] + y[R] + x[R];
+    }
+    __device__ __forceinline__ int center() const { return z[R] + y[R] + x[R]; }
+};
+
+template <typename T, typename P>
+__device__ __forceinline__ T ld(const P *p) {
+    return T(__ldg(p));
+}
+
+// First derivative along AX of field f at the point (weights already / h).
+template <int R, int AX, typename T, typename P>
+__device__ __forceinline__ T D1(const P *__restrict__ f, const Nbr<R> &nb, const Coef<T> &c) {
+    T s = T(0);
+#pragma unroll
+    for (int k = R; k >= 1; --k)
+        s = fma(c.d1[AX][k], ld<T>(f + nb.template at<AX>(k)) - ld<T>(f + nb.template at<AX>(-k)), s);
+    return s;
+}
+
+// Second derivative along AX (weights already / h^2).
+template <int R, int AX, typename T, typename P>
+__device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R> &nb, const Coef<T> &c) {
+    T s = c.d2[AX][0] * ld<T>(f + nb.center());
+#pragma unroll
+    for (int k = R; k >= 1; --k)
+        s = fma(c.d2[AX][k], ld<T>(f + nb.template at<AX>(k)) + ld<T>(f + nb.template at<AX>(-k)), s);
+    return s;
+}
+
+constexpr int BX = 32, BY = 8;
+
+// ---------------------------------------------------------------------------
+// k_prim: primitives and the point-wise momentum fluxes
+// ---------------------------------------------------------------------------
+template <typename S, typename T>
+__global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+    if (x >= a.d.nx || y >= a.d.ny) return;
+    const int i = (z * a.d.ny + y) * a.d.nx + x;
+    const S *Q = static_cast<const S *>(a.src);
+    const size_t qs = a.src_stride;
+    T *aux = static_cast<T *>(a.aux);
+    const size_t as = a.aux_stride;
+
+    const T rho = T(Q[i]), mx = T(Q[qs + i]), my = T(Q[2 * qs + i]), mz = T(Q[3 * qs + i]);
+    const T e = T(Q[4 * qs + i]);
+    const T rinv = T(1) / rho;
+    const T u = mx * rinv, v = my * rinv, w = mz * rinv;
+    const T ke = T(0.5) * (mx * u + my * v + mz * w);
+    const T p = T(a.ph.gm1) * (e - ke);
+    const T temp = T(a.ph.gM2) * p * rinv;
+    const T hmx = T(0.5) * mx, hmy = T(0.5) * my;
+    aux[A_U * as + i] = u;
+    aux[A_V * as + i] = v;
+    aux[A_W * as + i] = w;
+    aux[A_P * as + i] = p;
+    aux[A_T * as + i] = temp;
+    aux[A_PXX * as + i] = fma(hmx, u, p);
+    aux[A_PYY * as + i] = fma(hmy, v, p);
+    aux[A_PZZ * as + i] = fma(T(0.5) * mz, w, p);
+    aux[A_PXY * as + i] = hmx * v;
+    aux[A_PXZ * as + i] = hmx * w;
+    aux[A_PYZ * as + i] = hmy * w;
+}
+
+// ---------------------------------------------------------------------------
+// k_grad: velocity gradient -> div u, tau_ij, energy flux, viscous g-term
+// ---------------------------------------------------------------------------
+template <typename S, typename T, int R>
+__global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+    if (x >= a.d.nx || y >= a.d.ny) return;
+    Nbr<R> nb;
+    nb.init(x, y, z, a.d);
+    const int i = nb.center();
+    const Coef<T> &c = CoefPick<T>::get(a);
+    T *aux = static_cast<T *>(a.aux);
+    const size_t as = a.aux_stride;
+    const T *U = aux + A_U * as, *V = aux + A_V * as, *W = aux + A_W * as;
+
+    const T gxx = D1<R, 0>(U, nb, c), gxy = D1<R, 1>(U, nb, c), gxz = D1<R, 2>(U, nb, c);
+    const T gyx = D1<R, 0>(V, nb, c), gyy = D1<R, 1>(V, nb, c), gyz = D1<R, 2>(V, nb, c);
+    const T gzx = D1<R, 0>(W, nb, c), gzy = D1<R, 1>(W, nb, c), gzz = D1<R, 2>(W, nb, c);
+    const T div = gxx + gyy + gzz;
+    const T ir = T(a.ph.inv_re);
+    const T tdiv = T(2.0 / 3.0) * div;
+    const T txx = ir * (gxx + gxx - tdiv), tyy = ir * (gyy + gyy - tdiv), tzz = ir * (gzz + gzz - tdiv);
+    const T txy = ir * (gxy + gyx), txz = ir * (gxz + gzx), tyz = ir * (gyz + gzy);
+    const T u = aux[A_U * as + i], v = aux[A_V * as + i], w = aux[A_W * as + i];
+    const T p = aux[A_P * as + i];
+    const S *Q = static_cast<const S *>(a.src);
+    const T hE = fma(T(0.5), T(Q[4 * a.src_stride + i]), p);
+    aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
+    aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
+    aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
+    aux[A_DIV * as + i] = div;
+    const T ir3 = ir * T(1.0 / 3.0);
+    aux[A_PXX * as + i] -= ir3 * (gyy + gzz);
+    aux[A_PYY * as + i] -= ir3 * (gxx + gzz);
+    aux[A_PZZ * as + i] -= ir3 * (gxx + gyy);
+}
+
+// ---------------------------------------------------------------------------
+// k_resid: residual and RK update (MODE 0) or residual only (MODE 1)
+// ---------------------------------------------------------------------------
+template <typename S, typename T, int R, int MODE>
+__global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+    if (x >= a.d.nx || y >= a.d.ny) return;
+    Nbr<R> nb;
+    nb.init(x, y, z, a.d);
+    const int i = nb.center();
+    const Coef<T> &c = CoefPick<T>::get(a);
+    const S *Q = static_cast<const S *>(a.src);
+    const size_t qs = a.src_stride;
+    const T *aux = static_cast<const T *>(a.aux);
+    const size_t as = a.aux_stride;
+
+    const T u = aux[A_U * as + i], v = aux[A_V * as + i], w = aux[A_W * as + i];
+    const T div = aux[A_DIV * as + i];
+
+    T res[5];
+    // advective + dilatation half of the skew-symmetric form, per field
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const S *f = Q + m * qs;
+        const T dx = D1<R, 0>(f, nb, c), dy = D1<R, 1>(f, nb, c), dz = D1<R, 2>(f, nb, c);
+        res[m] = T(-0.5) * fma(u, dx, fma(v, dy, fma(w, dz, T(f[i]) * div)));
+        // mass flux d_j(m_j/2): m_j is field 1+j, differentiated along j
+        if (m == 1) res[0] = fma(T(-0.5), dx, res[0]);
+        if (m == 2) res[0] = fma(T(-0.5), dy, res[0]);
+        if (m == 3) res[0] = fma(T(-0.5), dz, res[0]);
+    }
+    // momentum fluxes
+    const T *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
+    const T *Pxy = aux + A_PXY * as, *Pxz = aux + A_PXZ * as, *Pyz = aux + A_PYZ * as;
+    res[1] -= D1<R, 0>(Pxx, nb, c) + D1<R, 1>(Pxy, nb, c) + D1<R, 2>(Pxz, nb, c);
+    res[2] -= D1<R, 0>(Pxy, nb, c) + D1<R, 1>(Pyy, nb, c) + D1<R, 2>(Pyz, nb, c);
+    res[3] -= D1<R, 0>(Pxz, nb, c) + D1<R, 1>(Pyz, nb, c) + D1<R, 2>(Pzz, nb, c);
+    // energy flux
+    res[4] -= D1<R, 0>(aux + A_FX * as, nb, c) + D1<R, 1>(aux + A_FY * as, nb, c) +
+              D1<R, 2>(aux + A_FZ * as, nb, c);
+    // viscous Laplacians: (1/Re)[sum_j L_j u_i + L_i u_i / 3]
+    const T ir = T(a.ph.inv_re), f43 = T(4.0 / 3.0);
+    {
+        const T *Uf = aux + A_U * as;
+        res[1] = fma(ir, fma(f43, D2<R, 0>(Uf, nb, c), D2<R, 1>(Uf, nb, c) + D2<R, 2>(Uf, nb, c)), res[1]);
+        const T *Vf = aux + A_V * as;
+        res[2] = fma(ir, fma(f43, D2<R, 1>(Vf, nb, c), D2<R, 0>(Vf, nb, c) + D2<R, 2>(Vf, nb, c)), res[2]);
+        const T *Wf = aux + A_W * as;
+        res[3] = fma(ir, fma(f43, D2<R, 2>(Wf, nb, c), D2<R, 0>(Wf, nb, c) + D2<R, 1>(Wf, nb, c)), res[3]);
+        const T *Tf = aux + A_T * as;
+        res[4] = fma(T(a.ph.kappa), D2<R, 0>(Tf, nb, c) + D2<R, 1>(Tf, nb, c) + D2<R, 2>(Tf, nb, c), res[4]);
+    }
+
+    if (MODE == 0) {
+        T *qo = static_cast<T *>(a.q_out);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const double Ui = a.U_in[m * a.u_stride + i];
+            const double Rm = double(res[m]);
+            a.U_out[m * a.u_stride + i] = fma(a.beta_dt, Rm, Ui);
+            if (qo) qo[m * a.q_stride + i] = T(fma(a.alpha_dt, Rm, Ui));
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) a.R_out[m * a.R_stride + i] = double(res[m]);
+    }
+}
+
+template <typename S, typename T, int R>
+cudaError_t launch_stage_typed(const StageArgs &a, int mode) {
+    dim3 blk(BX, BY, 1), grd((a.d.nx + BX - 1) / BX, (a.d.ny + BY - 1) / BY, a.d.nz);
+    if (a.ev) cudaEventRecord(a.ev[0], a.stream);
+    k_prim<S, T><<<grd, blk, 0, a.stream>>>(a);
+    if (a.ev) cudaEventRecord(a.ev[1], a.stream);
+    k_grad<S, T, R><<<grd, blk, 0, a.stream>>>(a);
+    if (a.ev) cudaEventRecord(a.ev[2], a.stream);
+    if (mode == 0)
+        k_resid<S, T, R, 0><<<grd, blk, 0, a.stream>>>(a);
+    else
+        k_resid<S, T, R, 1><<<grd, blk, 0, a.stream>>>(a);
+    if (a.ev) cudaEventRecord(a.ev[3], a.stream);
+    return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_stage(const StageArgs &a, int mode) {
+    if (a.precision == OSB_FP64) return launch_stage_typed<double, double, R>(a, mode);
+    if (a.src_is_f64) return launch_stage_typed<double, float, R>(a, mode);
+    return launch_stage_typed<float, float, R>(a, mode);
+}
+
+template <int R>
+cudaError_t stage_entry(const StageArgs &a) {
+    return launch_stage<R>(a, 0);
+}
+template <int R>
+cudaError_t residual_entry(const StageArgs &a) {
+    return launch_stage<R>(a, 1);
+}
+
+}  // namespace osb
+
+#define OSB_DEFINE_ORDER(ORDER)                                                 \
+    namespace osb {                                                            \
+    OrderKernels kernels_o##ORDER() {                                          \
+        return OrderKernels{ORDER, &stage_entry<ORDER / 2>, &residual_entry<ORDER / 2>}; \
+    }                                                                          \
+    }

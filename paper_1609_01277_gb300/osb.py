@@ -1,0 +1,235 @@
+"""Python binding of libosb (ctypes).  Argument marshalling only: every step of
+the time step runs in the library's CUDA kernels.  PyTorch supplies the device
+buffers and the stream.
+
+The library must be built (``python -m paper_1609_01277_gb300.build`` or
+``__graft_entry__.build()``); importing this module on a machine without it
+raises, and nothing here falls back to a CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+OSB_FP64, OSB_FP32 = 0, 1
+OSB_VISC_A, OSB_VISC_B = 0, 1
+STATUS = {0: "OSB_OK", 1: "OSB_ERR_INVALID_ARG", 2: "OSB_ERR_UNSUPPORTED", 3: "OSB_ERR_CUDA",
+          4: "OSB_ERR_NONFINITE", 5: "OSB_ERR_TIMEOUT", 6: "OSB_ERR_BUFFER"}
+
+# every entry point declared in include/osb.h
+EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_grid_destroy",
+           "osb_init_taylor_green", "osb_set_state", "osb_get_state", "osb_set_state_device",
+           "osb_get_state_device", "osb_residual", "osb_rk3_step", "osb_diagnostics",
+           "osb_batch_step", "osb_profile_start", "osb_profile_stop", "osb_status_string",
+           "osb_last_error")
+KERNEL_KINDS = ("prim", "grad", "resid")
+
+
+class OsbError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {detail}")
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("order", ctypes.c_int), ("precision", ctypes.c_int), ("visc_form", ctypes.c_int)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("Re", ctypes.c_double), ("Mach", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("Pr", ctypes.c_double), ("dt", ctypes.c_double)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("step", ctypes.c_longlong), ("ke", ctypes.c_double),
+                ("enstrophy", ctypes.c_double), ("total", ctypes.c_double * 5),
+                ("nonfinite", ctypes.c_longlong), ("max_cfl", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libosb and declare the signatures.  Raises if the library is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libosb is not built ({path}); run paper_1609_01277_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, sz, dp = ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)
+    D, P = ctypes.POINTER(GridDesc), ctypes.POINTER(Params)
+    L.osb_state_bytes.argtypes = [D]
+    L.osb_state_bytes.restype = sz
+    L.osb_workspace_bytes.argtypes = [D]
+    L.osb_workspace_bytes.restype = sz
+    L.osb_grid_create.argtypes = [D, P, vp, sz, vp, sz, vp, ctypes.POINTER(vp)]
+    L.osb_grid_destroy.argtypes = [vp]
+    L.osb_init_taylor_green.argtypes = [vp, vp, ctypes.c_double]
+    L.osb_set_state.argtypes = [vp, vp]
+    L.osb_get_state.argtypes = [vp, vp]
+    L.osb_set_state_device.argtypes = [vp, vp]
+    L.osb_get_state_device.argtypes = [vp, vp]
+    L.osb_residual.argtypes = [vp, vp]
+    L.osb_rk3_step.argtypes = [vp, ctypes.c_int]
+    L.osb_diagnostics.argtypes = [vp, ctypes.POINTER(Diag)]
+    L.osb_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
+    L.osb_profile_start.argtypes = [vp, ctypes.c_int]
+    L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.osb_status_string.argtypes = [ctypes.c_int]
+    L.osb_status_string.restype = ctypes.c_char_p
+    L.osb_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("osb_state_bytes", "osb_workspace_bytes", "osb_status_string", "osb_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def check(status: int, where: str) -> None:
+    if status != 0:
+        raise OsbError(status, where, load().osb_last_error().decode())
+
+
+@dataclass
+class Config:
+    nx: int
+    ny: int
+    nz: int
+    order: int = 4
+    precision: int = OSB_FP64
+    visc_form: int = OSB_VISC_A
+    Re: float = 1600.0
+    Mach: float = 0.1
+    gamma: float = 1.4
+    Pr: float = 0.71
+    dt: float = 3.385e-3
+
+    def desc(self) -> GridDesc:
+        return GridDesc(self.nx, self.ny, self.nz, self.order, self.precision, self.visc_form)
+
+    def params(self) -> Params:
+        return Params(self.Re, self.Mach, self.gamma, self.Pr, self.dt)
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def shape(self):
+        return (5, self.nz, self.ny, self.nx)
+
+
+class Grid:
+    """One periodic grid on the current CUDA device, advanced on one stream."""
+
+    def __init__(self, cfg: Config, stream=None, device=None):
+        import torch
+        L = load()
+        self.cfg = cfg
+        self._torch = torch
+        device = torch.device(device or "cuda")
+        d = cfg.desc()
+        sb = L.osb_state_bytes(ctypes.byref(d))
+        wb = L.osb_workspace_bytes(ctypes.byref(d))
+        if sb == 0 or wb == 0:
+            raise OsbError(1, "osb_*_bytes", "invalid grid descriptor")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.state = torch.empty(sb, dtype=torch.uint8, device=device)
+        self.workspace = torch.empty(wb, dtype=torch.uint8, device=device)
+        h = ctypes.c_void_p()
+        p = cfg.params()
+        check(L.osb_grid_create(ctypes.byref(d), ctypes.byref(p), self.state.data_ptr(), sb,
+                                self.workspace.data_ptr(), wb, self.stream.cuda_stream, ctypes.byref(h)),
+              "osb_grid_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().osb_grid_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state ----------------------------------------------------------------
+    def init_taylor_green(self, noise=None, amp: float = 0.0) -> None:
+        """noise: None, or a (3, nz, ny, nx) float64 array (numpy or CUDA tensor)."""
+        torch = self._torch
+        ptr = None
+        if noise is not None:
+            t = torch.as_tensor(noise, dtype=torch.float64)
+            t = t.to(self.state.device).contiguous()
+            if t.numel() != 3 * self.cfg.n:
+                raise ValueError("noise must hold 3*N values")
+            self._noise = t  # keep alive until the kernel has run
+            ptr = t.data_ptr()
+        check(load().osb_init_taylor_green(self.handle, ptr, float(amp)), "osb_init_taylor_green")
+
+    def set_state(self, Q: np.ndarray) -> None:
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        if Q.size != 5 * self.cfg.n:
+            raise ValueError("state must hold 5*N values")
+        check(load().osb_set_state(self.handle, Q.ctypes.data), "osb_set_state")
+
+    def get_state(self, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.cfg.shape, dtype=np.float64)
+        check(load().osb_get_state(self.handle, out.ctypes.data), "osb_get_state")
+        return out
+
+    def set_state_device(self, Q) -> None:
+        self._src = Q.contiguous()
+        check(load().osb_set_state_device(self.handle, self._src.data_ptr()), "osb_set_state_device")
+
+    def get_state_device(self, out=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty(self.cfg.shape, dtype=torch.float64, device=self.state.device)
+        check(load().osb_get_state_device(self.handle, out.data_ptr()), "osb_get_state_device")
+        return out
+
+    # -- compute --------------------------------------------------------------
+    def residual(self, out=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty(self.cfg.shape, dtype=torch.float64, device=self.state.device)
+        check(load().osb_residual(self.handle, out.data_ptr()), "osb_residual")
+        return out
+
+    def step(self, nsteps: int = 1) -> None:
+        check(load().osb_rk3_step(self.handle, int(nsteps)), "osb_rk3_step")
+
+    def profile_start(self, max_stages: int) -> None:
+        check(load().osb_profile_start(self.handle, int(max_stages)), "osb_profile_start")
+
+    def profile_stop(self) -> dict:
+        ms = (ctypes.c_double * 3)()
+        n = (ctypes.c_longlong * 3)()
+        check(load().osb_profile_stop(self.handle, ms, n), "osb_profile_stop")
+        return {k: dict(total_ms=ms[i], launches=n[i]) for i, k in enumerate(KERNEL_KINDS)}
+
+    def diagnostics(self, raise_nonfinite: bool = True) -> dict:
+        d = Diag()
+        st = load().osb_diagnostics(self.handle, ctypes.byref(d))
+        if st != 0 and (raise_nonfinite or st != 4):
+            check(st, "osb_diagnostics")
+        return dict(t=d.t, step=d.step, ke=d.ke, enstrophy=d.enstrophy, total=list(d.total),
+                    nonfinite=d.nonfinite, max_cfl=d.max_cfl, status=st)
+
+
+def batch_step(grids, nsteps: int) -> None:
+    arr = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
+    check(load().osb_batch_step(arr, len(grids), int(nsteps)), "osb_batch_step")

@@ -1,0 +1,241 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances: FP64 results must match the oracle to a relative L2 of 1e-12 per
+field after N steps (the bar of the FP64 path).  The residual itself is held
+to the same 1e-12.  The FP32 path is held to a bound derived from FP32
+rounding (see test_fp32_*).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1609_01277_gb300 import inputs
+from tests.helpers import conserved, rel_l2, rel_l2_fields
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def osb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_01277_gb300 import build
+    build.build()
+    from paper_1609_01277_gb300 import osb as m
+    m.load()
+    return m
+
+
+def _grid(osb, nx, ny, nz, **kw):
+    return osb.Grid(osb.Config(nx, ny, nz, **kw))
+
+
+def _case(nx, ny, nz, **kw):
+    kw = {k: v for k, v in kw.items() if k != "precision"}
+    return orc.Case(nx, ny, nz, **kw)
+
+
+def _random_state(nx, ny, nz, seed, gamma=1.4):
+    return conserved(*inputs.smooth_primitive_state(nx, ny, nz, seed), gamma=gamma)
+
+
+# --------------------------------------------------------------------------
+def test_initial_state_matches_oracle(osb):
+    for (nx, ny, nz) in [(8, 8, 8), (32, 32, 32), (17, 12, 9)]:
+        g = _grid(osb, nx, ny, nz)
+        g.init_taylor_green()
+        Q = g.get_state()
+        Qo = orc.tgv_init(_case(nx, ny, nz))
+        assert rel_l2(Q, Qo) < 1e-15
+        noise = inputs.gaussian_noise(nx, ny, nz, seed=1234)
+        g.init_taylor_green(noise, 1e-4)
+        Qo = orc.tgv_init(_case(nx, ny, nz), noise, 1e-4)
+        assert rel_l2(g.get_state(), Qo) < 1e-15
+
+
+@pytest.mark.parametrize("n,order", [(32, 4), (8, 4), (24, 8), (16, 2)])
+def test_initial_diagnostics_closed_form(osb, n, order):
+    g = _grid(osb, n, n, n, order=order)
+    g.init_taylor_green()
+    dg = g.diagnostics()
+    c, _ = orc.fd_coeffs(order)
+    h = 2 * math.pi / n
+    k1 = sum(2 * c[m] * math.sin(m * h) for m in range(1, order // 2 + 1)) / h
+    gM2 = 1.4 * 0.01
+    assert dg["ke"] == pytest.approx(0.125, rel=1e-13)
+    assert dg["enstrophy"] == pytest.approx(k1 ** 2 * (3 / 8 - 5 * gM2 / 128), rel=1e-13)
+    assert dg["total"][0] == pytest.approx(1.0, rel=1e-13)
+    assert dg["nonfinite"] == 0
+
+
+def test_diagnostics_match_oracle_on_random_state(osb):
+    nx, ny, nz = 20, 14, 11
+    Q = _random_state(nx, ny, nz, seed=9)
+    g = _grid(osb, nx, ny, nz, order=6, dt=1e-3)
+    g.set_state(Q)
+    dg = g.diagnostics()
+    do = orc.diagnostics(_case(nx, ny, nz, order=6, dt=1e-3), Q)
+    assert dg["ke"] == pytest.approx(do["ke"], rel=1e-13)
+    assert dg["enstrophy"] == pytest.approx(do["enstrophy"], rel=1e-13)
+    for m, k in enumerate(("rho", "rhou0", "rhou1", "rhou2", "rhoE")):
+        assert dg["total"][m] == pytest.approx(do[k], rel=1e-12, abs=1e-15)
+    assert dg["max_cfl"] == pytest.approx(do["max_cfl"], rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [2, 4, 6, 8, 10, 12])
+@pytest.mark.parametrize("dims", [(16, 16, 16), (37, 20, 9), (8, 8, 8)])
+def test_residual_matches_oracle(osb, order, dims):
+    """Several 32x8 tiles plus ragged tails in x and y; 8^3 wraps the widest
+    stencils around the box."""
+    nx, ny, nz = dims
+    Q = _random_state(nx, ny, nz, seed=order + nx)
+    g = _grid(osb, nx, ny, nz, order=order, Re=100.0)
+    g.set_state(Q)
+    R = g.residual().cpu().numpy()
+    Ro = orc.residual(_case(nx, ny, nz, order=order, Re=100.0), Q)
+    for m, err in rel_l2_fields(R, Ro).items():
+        assert err < TOL64, (m, err)
+
+
+@pytest.mark.parametrize("n,order,steps", [(32, 4, 20), (8, 4, 10), (8, 8, 10), (16, 6, 10), (48, 8, 5)])
+def test_tgv_steps_match_oracle(osb, n, order, steps):
+    """The small Taylor-Green case (32^3, 4th order, 20 steps of dt = 3.385e-3)
+    and variants: rel-L2 per field <= 1e-12."""
+    g = _grid(osb, n, n, n, order=order)
+    g.init_taylor_green()
+    g.step(steps)
+    Q = g.get_state()
+    case = _case(n, n, n, order=order)
+    Qo = orc.rk3_step(case, orc.tgv_init(case), steps)
+    for m, err in rel_l2_fields(Q, Qo).items():
+        assert err < TOL64, (m, err)
+
+
+def test_noisy_nonCubic_steps_match_oracle(osb):
+    nx, ny, nz = 40, 24, 18
+    noise = inputs.gaussian_noise(nx, ny, nz, seed=1234)
+    g = _grid(osb, nx, ny, nz, order=8, dt=1e-3)
+    g.init_taylor_green(noise, 1e-4)
+    g.step(6)
+    case = _case(nx, ny, nz, order=8, dt=1e-3)
+    Qo = orc.rk3_step(case, orc.tgv_init(case, noise, 1e-4), 6)
+    for m, err in rel_l2_fields(g.get_state(), Qo).items():
+        assert err < TOL64, (m, err)
+
+
+def test_random_state_steps_match_oracle(osb):
+    nx, ny, nz = 24, 16, 20
+    Q0 = _random_state(nx, ny, nz, seed=5)
+    g = _grid(osb, nx, ny, nz, order=4, Re=50.0, dt=1e-3)
+    g.set_state(Q0)
+    g.step(4)
+    Qo = orc.rk3_step(_case(nx, ny, nz, order=4, Re=50.0, dt=1e-3), Q0, 4)
+    for m, err in rel_l2_fields(g.get_state(), Qo).items():
+        assert err < TOL64, (m, err)
+
+
+# --------------------------------------------------------------------------
+def test_conservation_on_gpu(osb):
+    n = 32
+    g = _grid(osb, n, n, n, order=8)
+    noise = inputs.gaussian_noise(n, n, n, seed=3)
+    g.init_taylor_green(noise, 1e-2)
+    d0 = g.diagnostics()
+    g.step(30)
+    d1 = g.diagnostics()
+    for m in range(5):
+        scale = max(abs(d0["total"][m]), 1.0)
+        assert abs(d1["total"][m] - d0["total"][m]) < 1e-13 * 30 * 3 * scale
+
+
+def test_checkpoint_restart_is_bitwise(osb):
+    n = 16
+    a = _grid(osb, n, n, n)
+    a.init_taylor_green()
+    a.step(6)
+    full = a.get_state()
+    b = _grid(osb, n, n, n)
+    b.init_taylor_green()
+    b.step(3)
+    mid = b.get_state()
+    c = _grid(osb, n, n, n)
+    c.set_state(mid)
+    c.step(3)
+    assert np.array_equal(c.get_state(), full)
+
+
+def test_runs_are_deterministic(osb):
+    n = 24
+    out = []
+    for _ in range(2):
+        g = _grid(osb, n, n, n, order=4)
+        g.init_taylor_green(inputs.gaussian_noise(n, n, n, seed=2), 1e-3)
+        g.step(5)
+        out.append((g.get_state(), g.diagnostics()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1]["ke"] == out[1][1]["ke"] and out[0][1]["enstrophy"] == out[1][1]["enstrophy"]
+
+
+def test_nonfinite_state_is_reported(osb):
+    n = 8
+    g = _grid(osb, n, n, n)
+    Q = orc.tgv_init(_case(n, n, n))
+    Q[3, 1, 2, 3] = np.nan
+    g.set_state(Q)
+    dg = g.diagnostics(raise_nonfinite=False)
+    assert dg["status"] == 4 and dg["nonfinite"] == 1
+    with pytest.raises(osb.OsbError):
+        g.diagnostics()
+
+
+def test_batch_step_matches_single_grids(osb):
+    sizes = [(16, 16, 16, 1600.0, 0.1), (24, 24, 24, 400.0, 0.2), (12, 12, 12, 3000.0, 0.05)]
+    singles, batch = [], []
+    for (nx, ny, nz, Re, M) in sizes:
+        for lst in (singles, batch):
+            g = _grid(osb, nx, ny, nz, Re=Re, Mach=M, dt=1e-3)
+            g.init_taylor_green()
+            lst.append(g)
+    for g in singles:
+        g.step(4)
+    osb.batch_step(batch, 4)
+    for a, b in zip(singles, batch):
+        assert np.array_equal(a.get_state(), b.get_state())
+
+
+# --------------------------------------------------------------------------
+# FP32 path: stencils in FP32, U accumulator and reductions in FP64
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [4, 8])
+def test_fp32_residual_error_is_fp32_rounding(osb, order):
+    """FP32 residual vs the FP64 oracle: the error is FP32 rounding of the
+    inputs and intermediates amplified by the stencil cancellation (~1/h),
+    so rel-L2 stays below ~1e3 * 2^-24 at these sizes."""
+    n = 24
+    Q = _random_state(n, n, n, seed=17)
+    g = _grid(osb, n, n, n, order=order, precision=osb.OSB_FP32, Re=100.0)
+    g.set_state(Q)
+    R = g.residual().cpu().numpy()
+    Ro = orc.residual(_case(n, n, n, order=order, Re=100.0), Q)
+    for m, err in rel_l2_fields(R, Ro).items():
+        assert err < 1e3 * 2.0 ** -24, (m, err)
+
+
+def test_fp32_tgv_steps_close_to_oracle(osb):
+    n, steps = 32, 20
+    g = _grid(osb, n, n, n, order=4, precision=osb.OSB_FP32)
+    g.init_taylor_green()
+    g.step(steps)
+    case = _case(n, n, n, order=4)
+    Qo = orc.rk3_step(case, orc.tgv_init(case), steps)
+    errs = rel_l2_fields(g.get_state(), Qo)
+    for m, err in errs.items():
+        assert err < 1e-5, (m, err)
