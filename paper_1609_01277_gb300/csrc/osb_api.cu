@@ -131,6 +131,7 @@ StageArgs base_args(const osb_grid *g) {
     a.c64 = g->c64;
     a.c32 = g->c32;
     a.precision = g->desc.precision;
+    a.visc_form = g->desc.visc_form;
     a.aux = g->aux;
     a.aux_stride = g->aux_stride;
     a.u_stride = g->u_stride;
@@ -140,6 +141,40 @@ StageArgs base_args(const osb_grid *g) {
 }
 
 }  // namespace
+
+namespace osb {
+
+Phys make_phys(const osb_params &prm) {
+    Phys ph;
+    ph.Re = prm.Re;
+    ph.Mach = prm.Mach;
+    ph.gamma = prm.gamma;
+    ph.Pr = prm.Pr;
+    ph.inv_re = 1.0 / prm.Re;
+    ph.kappa = 1.0 / ((prm.gamma - 1.0) * prm.Mach * prm.Mach * prm.Pr * prm.Re);
+    ph.gm1 = prm.gamma - 1.0;
+    ph.gM2 = prm.gamma * prm.Mach * prm.Mach;
+    return ph;
+}
+
+void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float> *c32) {
+    double c[MAXR + 1], dd[MAXR + 1];
+    fd_weights(order, c, dd);
+    const int dims[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; ++a) {
+        const double h = 2.0 * M_PI / dims[a];
+        for (int k = 0; k <= MAXR; ++k) {
+            c64->d1[a][k] = c[k] / h;
+            c64->d2[a][k] = dd[k] / (h * h);
+            c32->d1[a][k] = (float)c64->d1[a][k];
+            c32->d2[a][k] = (float)c64->d2[a][k];
+        }
+    }
+}
+
+void set_last_error(const char *msg) { g_err = msg; }
+
+}  // namespace osb
 
 extern "C" {
 
@@ -169,7 +204,6 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     if (!desc_ok(desc)) return fail(OSB_ERR_INVALID_ARG, "invalid grid descriptor");
     if (!prm || !(prm->Re > 0) || !(prm->Mach > 0) || !(prm->Pr > 0) || !(prm->dt > 0) || !(prm->gamma > 1))
         return fail(OSB_ERR_INVALID_ARG, "invalid physical parameters");
-    if (desc->visc_form != OSB_VISC_A) return fail(OSB_ERR_UNSUPPORTED, "viscous work form B is not built");
     OrderKernels K = kernels_for(desc->order);
     if (!K.stage) return fail(OSB_ERR_UNSUPPORTED, "order not instantiated");
     if (!state_dev || !ws_dev) return fail(OSB_ERR_INVALID_ARG, "NULL device buffer");
@@ -185,26 +219,8 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     g->prm = *prm;
     const size_t n = npoints(desc);
     g->d = Dims{desc->nx, desc->ny, desc->nz, (int)n};
-    g->ph.Re = prm->Re;
-    g->ph.Mach = prm->Mach;
-    g->ph.gamma = prm->gamma;
-    g->ph.Pr = prm->Pr;
-    g->ph.inv_re = 1.0 / prm->Re;
-    g->ph.kappa = 1.0 / ((prm->gamma - 1.0) * prm->Mach * prm->Mach * prm->Pr * prm->Re);
-    g->ph.gm1 = prm->gamma - 1.0;
-    g->ph.gM2 = prm->gamma * prm->Mach * prm->Mach;
-    double c[MAXR + 1], dd[MAXR + 1];
-    fd_weights(desc->order, c, dd);
-    const int dims[3] = {desc->nx, desc->ny, desc->nz};
-    for (int a = 0; a < 3; ++a) {
-        const double h = 2.0 * M_PI / dims[a];
-        for (int k = 0; k <= MAXR; ++k) {
-            g->c64.d1[a][k] = c[k] / h;
-            g->c64.d2[a][k] = dd[k] / (h * h);
-            g->c32.d1[a][k] = (float)g->c64.d1[a][k];
-            g->c32.d2[a][k] = (float)g->c64.d2[a][k];
-        }
-    }
+    g->ph = make_phys(*prm);
+    make_coefs(desc->order, desc->nx, desc->ny, desc->nz, &g->c64, &g->c32);
     g->K = K;
     g->state = (char *)state_dev;
     g->ws = (char *)ws_dev;

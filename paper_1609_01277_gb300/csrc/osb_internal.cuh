@@ -27,6 +27,8 @@ enum Aux {
     A_PXY, A_PXZ, A_PYZ,      // momentum flux Phi_ij = rho u_i u_j/2 (i != j)
     A_FX, A_FY, A_FZ,         // energy flux F_j = (rho E/2 + p) u_j - u_i tau_ij
     A_DIV,                    // d_k u_k
+    A_GX, A_GY, A_GZ,         // g_i = d_k u_k - d_i u_i        (viscous work form B only)
+    A_TG,                     // tau_ij d_j u_i                  (viscous work form B only)
     NAUX
 };
 
@@ -64,6 +66,7 @@ struct StageArgs {
     Coef<double> c64;
     Coef<float> c32;
     int precision;          // OSB_FP64 / OSB_FP32
+    int visc_form;          // OSB_VISC_A / OSB_VISC_B
     const void *src;        // stencil source q_{k-1}
     int src_is_f64;         // 1: src holds doubles (U register), 0: type T
     size_t src_stride;      // elements between fields of src
@@ -96,6 +99,11 @@ OrderKernels kernels_o6();
 OrderKernels kernels_o8();
 OrderKernels kernels_o10();
 OrderKernels kernels_o12();
+
+// Host helpers shared by the translation units (defined in osb_api.cu).
+Phys make_phys(const osb_params &prm);
+void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float> *c32);
+void set_last_error(const char *msg);
 
 // Misc kernels (init, diagnostics).
 cudaError_t launch_init_tgv(const Dims &d, const Phys &ph, double *U, size_t stride,

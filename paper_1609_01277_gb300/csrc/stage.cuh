@@ -23,6 +23,10 @@
 // This is the skew-symmetric convective form, the pressure terms, d_j tau_ij
 // (Laplacian by L, mixed terms as D_i(D_k u_k)) and the conservative viscous
 // work and heat flux, regrouped by linearity of D_j.
+// Viscous work form B (template VB) instead keeps F_j = (e/2 + p) u_j and
+// Phi_ii = m_i u_i/2 + p, and adds u_i V_i + tau_ij D_j u_i to R_e, where
+// V_i = (1/Re)[sum_j L_j u_i + L_i u_i/3 + D_i g_i/3] is the viscous momentum
+// term (the product rule applied to d_j(u_i tau_ij)).
 #pragma once
 
 #include "osb_internal.cuh"
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
 // ---------------------------------------------------------------------------
 // k_grad: velocity gradient -> div u, tau_ij, energy flux, viscous g-term
 // ---------------------------------------------------------------------------
-template <typename S, typename T, int R>
+template <typename S, typename T, int R, bool VB>
 __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
     if (x >= a.d.nx || y >= a.d.ny) return;
@@ -156,20 +160,31 @@ __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
     const T p = aux[A_P * as + i];
     const S *Q = static_cast<const S *>(a.src);
     const T hE = fma(T(0.5), T(Q[4 * a.src_stride + i]), p);
-    aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
-    aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
-    aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
     aux[A_DIV * as + i] = div;
-    const T ir3 = ir * T(1.0 / 3.0);
-    aux[A_PXX * as + i] -= ir3 * (gyy + gzz);
-    aux[A_PYY * as + i] -= ir3 * (gxx + gzz);
-    aux[A_PZZ * as + i] -= ir3 * (gxx + gyy);
+    if (!VB) {
+        aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
+        aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
+        aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
+        const T ir3 = ir * T(1.0 / 3.0);
+        aux[A_PXX * as + i] -= ir3 * (gyy + gzz);
+        aux[A_PYY * as + i] -= ir3 * (gxx + gzz);
+        aux[A_PZZ * as + i] -= ir3 * (gxx + gyy);
+    } else {
+        aux[A_FX * as + i] = hE * u;
+        aux[A_FY * as + i] = hE * v;
+        aux[A_FZ * as + i] = hE * w;
+        aux[A_GX * as + i] = gyy + gzz;
+        aux[A_GY * as + i] = gxx + gzz;
+        aux[A_GZ * as + i] = gxx + gyy;
+        aux[A_TG * as + i] = txx * gxx + tyy * gyy + tzz * gzz + txy * (gxy + gyx) + txz * (gxz + gzx) +
+                             tyz * (gyz + gzy);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // k_resid: residual and RK update (MODE 0) or residual only (MODE 1)
 // ---------------------------------------------------------------------------
-template <typename S, typename T, int R, int MODE>
+template <typename S, typename T, int R, int MODE, bool VB>
 __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
     if (x >= a.d.nx || y >= a.d.ny) return;
@@ -209,12 +224,21 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     // viscous Laplacians: (1/Re)[sum_j L_j u_i + L_i u_i / 3]
     const T ir = T(a.ph.inv_re), f43 = T(4.0 / 3.0);
     {
-        const T *Uf = aux + A_U * as;
-        res[1] = fma(ir, fma(f43, D2<R, 0>(Uf, nb, c), D2<R, 1>(Uf, nb, c) + D2<R, 2>(Uf, nb, c)), res[1]);
-        const T *Vf = aux + A_V * as;
-        res[2] = fma(ir, fma(f43, D2<R, 1>(Vf, nb, c), D2<R, 0>(Vf, nb, c) + D2<R, 2>(Vf, nb, c)), res[2]);
-        const T *Wf = aux + A_W * as;
-        res[3] = fma(ir, fma(f43, D2<R, 2>(Wf, nb, c), D2<R, 0>(Wf, nb, c) + D2<R, 1>(Wf, nb, c)), res[3]);
+        const T *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as;
+        T vx = ir * fma(f43, D2<R, 0>(Uf, nb, c), D2<R, 1>(Uf, nb, c) + D2<R, 2>(Uf, nb, c));
+        T vy = ir * fma(f43, D2<R, 1>(Vf, nb, c), D2<R, 0>(Vf, nb, c) + D2<R, 2>(Vf, nb, c));
+        T vz = ir * fma(f43, D2<R, 2>(Wf, nb, c), D2<R, 0>(Wf, nb, c) + D2<R, 1>(Wf, nb, c));
+        if (VB) {
+            // the D_i g_i / 3 part of the viscous momentum term, kept separate
+            const T ir3 = ir * T(1.0 / 3.0);
+            vx = fma(ir3, D1<R, 0>(aux + A_GX * as, nb, c), vx);
+            vy = fma(ir3, D1<R, 1>(aux + A_GY * as, nb, c), vy);
+            vz = fma(ir3, D1<R, 2>(aux + A_GZ * as, nb, c), vz);
+            res[4] += fma(u, vx, fma(v, vy, fma(w, vz, aux[A_TG * as + i])));
+        }
+        res[1] += vx;
+        res[2] += vy;
+        res[3] += vz;
         const T *Tf = aux + A_T * as;
         res[4] = fma(T(a.ph.kappa), D2<R, 0>(Tf, nb, c) + D2<R, 1>(Tf, nb, c) + D2<R, 2>(Tf, nb, c), res[4]);
     }
@@ -234,27 +258,33 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     }
 }
 
-template <typename S, typename T, int R>
+template <typename S, typename T, int R, bool VB>
 cudaError_t launch_stage_typed(const StageArgs &a, int mode) {
     dim3 blk(BX, BY, 1), grd((a.d.nx + BX - 1) / BX, (a.d.ny + BY - 1) / BY, a.d.nz);
     if (a.ev) cudaEventRecord(a.ev[0], a.stream);
     k_prim<S, T><<<grd, blk, 0, a.stream>>>(a);
     if (a.ev) cudaEventRecord(a.ev[1], a.stream);
-    k_grad<S, T, R><<<grd, blk, 0, a.stream>>>(a);
+    k_grad<S, T, R, VB><<<grd, blk, 0, a.stream>>>(a);
     if (a.ev) cudaEventRecord(a.ev[2], a.stream);
     if (mode == 0)
-        k_resid<S, T, R, 0><<<grd, blk, 0, a.stream>>>(a);
+        k_resid<S, T, R, 0, VB><<<grd, blk, 0, a.stream>>>(a);
     else
-        k_resid<S, T, R, 1><<<grd, blk, 0, a.stream>>>(a);
+        k_resid<S, T, R, 1, VB><<<grd, blk, 0, a.stream>>>(a);
     if (a.ev) cudaEventRecord(a.ev[3], a.stream);
     return cudaGetLastError();
 }
 
+template <typename S, typename T, int R>
+cudaError_t launch_stage_form(const StageArgs &a, int mode) {
+    if (a.visc_form == OSB_VISC_B) return launch_stage_typed<S, T, R, true>(a, mode);
+    return launch_stage_typed<S, T, R, false>(a, mode);
+}
+
 template <int R>
 cudaError_t launch_stage(const StageArgs &a, int mode) {
-    if (a.precision == OSB_FP64) return launch_stage_typed<double, double, R>(a, mode);
-    if (a.src_is_f64) return launch_stage_typed<double, float, R>(a, mode);
-    return launch_stage_typed<float, float, R>(a, mode);
+    if (a.precision == OSB_FP64) return launch_stage_form<double, double, R>(a, mode);
+    if (a.src_is_f64) return launch_stage_form<double, float, R>(a, mode);
+    return launch_stage_form<float, float, R>(a, mode);
 }
 
 template <int R>
