@@ -151,6 +151,35 @@ osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
  * a bounded device-side wait gave up. */
 osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps);
 
+/* Diagnostics of a caller-provided state without any device allocation and
+ * without a grid object.  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory at the point where they need
+ * the diagnostics -- for example code running while a stream is captured into
+ * a CUDA graph in global capture mode (where cudaMalloc is an error that
+ * invalidates the capture), loops that must not take the implicit device
+ * synchronisation an allocation can cause, or hosts whose device memory is
+ * entirely pre-reserved by their own allocator.
+ *
+ *  Q_dev:   device, 5*nx*ny*nz FP64 values in the conserved layout above (no
+ *           padding between fields), caller-owned, read only.
+ *  out_dev: device, 9 FP64 values, caller-owned, written: ke, enstrophy,
+ *           total[0..4], the non-finite point count (as a double), max_cfl --
+ *           the same quantities as osb_diag.
+ *  params:  gamma, Mach and dt are used (gamma > 1, Mach > 0, dt > 0).
+ *  cuda_stream: stream the two kernels run on; the call does not synchronise.
+ * Scratch: a fixed device array of 1216 partial-sum records (155,648 bytes)
+ * inside the library, held on every device that loads the library until the
+ * process exits.  Every admissible grid (nx*ny*nz < 2^31, each >= 1) fits it;
+ * larger or invalid sizes are rejected with OSB_ERR_INVALID_ARG before any GPU
+ * work.  The first call on a device looks up the array's device address (no
+ * allocation); make that first call before any stream capture begins.  All
+ * calls share the one array, so calls whose kernels overlap on the GPU (for
+ * example on two streams at once) race and give wrong results; serialise them.
+ * No allocation of any kind: no cudaMalloc, cudaFree or allocating library
+ * routine is called. */
+osb_status osb_diagnostics_noalloc(const double *Q_dev, int nx, int ny, int nz, int order,
+                                   const osb_params *params, double *out_dev, void *cuda_stream);
+
 /* Per-kernel timing (tooling, no counterpart in the paper).  profile_start
  * creates 4 CUDA events per stage for up to max_stages stage launches; each
  * subsequent RK stage records them around its three kernels (primitives,

@@ -1,6 +1,8 @@
 // misc.cu -- Taylor-Green initial state and FP64 diagnostics reductions.
 #include <math.h>
 
+#include <mutex>
+
 #include "stage.cuh"
 
 namespace osb {
@@ -179,4 +181,88 @@ cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const C
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free diagnostics: the same two kernels, with the per-block
+// partial sums in a fixed device array that the library itself owns.
+//
+// Scratch: one record of DIAG_STRIDE doubles per block of the first kernel.
+// That kernel is launched with at most DIAG_MAX_BLOCKS (1216) blocks whatever
+// the grid size (grid-stride loop), so 1216 records (155,648 bytes) serve
+// every admissible grid.  Every record that the second kernel reads is written
+// by the first kernel of the same call, so nothing has to be cleared between
+// calls.  The array lives in each device's memory for as long as the library
+// is loaded; every call shares it.
+// ---------------------------------------------------------------------------
+constexpr int NOALLOC_RECORDS = DIAG_MAX_BLOCKS;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_RECORDS * DIAG_STRIDE];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static double *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
+
+// Device address of the scratch array on the current device.  In host code
+// the name g_noalloc_scratch is only a host-side stand-in, so the address is
+// looked up once per device (with that device current) and cached.
+static cudaError_t noalloc_scratch(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
 }  // namespace osb
+
+extern "C" osb_status osb_diagnostics_noalloc(const double *Q_dev, int nx, int ny, int nz, int order,
+                                              const osb_params *params, double *out_dev, void *cuda_stream) {
+    using namespace osb;
+    if (!Q_dev || !out_dev || !params) {
+        set_last_error("osb_diagnostics_noalloc: NULL argument");
+        return OSB_ERR_INVALID_ARG;
+    }
+    if (((uintptr_t)Q_dev & 7) || ((uintptr_t)out_dev & 7)) {
+        set_last_error("osb_diagnostics_noalloc: device pointers must be 8-byte aligned");
+        return OSB_ERR_BUFFER;
+    }
+    if (nx < 1 || ny < 1 || nz < 1 || order < 2 || order > 12 || (order & 1)) {
+        set_last_error("osb_diagnostics_noalloc: sizes must be >= 1 and order even in 2..12");
+        return OSB_ERR_INVALID_ARG;
+    }
+    if ((long long)nx * ny * nz > 0x7fffffffLL) {
+        set_last_error("osb_diagnostics_noalloc: grid too large (nx*ny*nz must be below 2^31)");
+        return OSB_ERR_INVALID_ARG;
+    }
+    if (!(params->gamma > 1) || !(params->Mach > 0) || !(params->dt > 0)) {
+        set_last_error("osb_diagnostics_noalloc: need gamma > 1, Mach > 0, dt > 0");
+        return OSB_ERR_INVALID_ARG;
+    }
+    const Dims d{nx, ny, nz, nx * ny * nz};
+    if (diag_num_partials(d) > NOALLOC_RECORDS) {
+        set_last_error("osb_diagnostics_noalloc: grid needs more partial records than the fixed scratch holds");
+        return OSB_ERR_BUFFER;
+    }
+    double *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) {
+        set_last_error("osb_diagnostics_noalloc: cudaGetSymbolAddress of the scratch array failed");
+        return OSB_ERR_CUDA;
+    }
+    Coef<double> c64;
+    Coef<float> c32;
+    make_coefs(order, nx, ny, nz, &c64, &c32);
+    e = launch_diagnostics(d, make_phys(*params), order, c64, params->dt, Q_dev, (size_t)d.n, scratch,
+                           NOALLOC_RECORDS, out_dev, (cudaStream_t)cuda_stream);
+    if (e != cudaSuccess) {
+        set_last_error("osb_diagnostics_noalloc: kernel launch failed");
+        return OSB_ERR_CUDA;
+    }
+    return OSB_OK;
+}

@@ -27,8 +27,8 @@ STATUS = {0: "OSB_OK", 1: "OSB_ERR_INVALID_ARG", 2: "OSB_ERR_UNSUPPORTED", 3: "O
 EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_grid_destroy",
            "osb_init_taylor_green", "osb_set_state", "osb_get_state", "osb_set_state_device",
            "osb_get_state_device", "osb_residual", "osb_rk3_step", "osb_diagnostics",
-           "osb_batch_step", "osb_profile_start", "osb_profile_stop", "osb_status_string",
-           "osb_last_error")
+           "osb_batch_step", "osb_diagnostics_noalloc", "osb_profile_start", "osb_profile_stop",
+           "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
 
@@ -83,6 +83,7 @@ def load(path: str | None = None):
     L.osb_rk3_step.argtypes = [vp, ctypes.c_int]
     L.osb_diagnostics.argtypes = [vp, ctypes.POINTER(Diag)]
     L.osb_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
+    L.osb_diagnostics_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, vp, vp]
     L.osb_profile_start.argtypes = [vp, ctypes.c_int]
     L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.osb_status_string.argtypes = [ctypes.c_int]
@@ -228,6 +229,18 @@ class Grid:
             check(st, "osb_diagnostics")
         return dict(t=d.t, step=d.step, ke=d.ke, enstrophy=d.enstrophy, total=list(d.total),
                     nonfinite=d.nonfinite, max_cfl=d.max_cfl, status=st)
+
+
+def diagnostics_noalloc(Q_dev, cfg: Config, out_dev, stream=None) -> None:
+    """Diagnostics of a caller-owned device state (5*N FP64, no padding) into a
+    caller-owned device array of 9 FP64 values, with no device allocation
+    (for callers that cannot allocate at that point, e.g. during a global-mode
+    stream capture).  Stream-ordered; the caller synchronises."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    p = cfg.params()
+    check(load().osb_diagnostics_noalloc(Q_dev.data_ptr(), cfg.nx, cfg.ny, cfg.nz, cfg.order, ctypes.byref(p),
+                                         out_dev.data_ptr(), st.cuda_stream), "osb_diagnostics_noalloc")
 
 
 def batch_step(grids, nsteps: int) -> None:

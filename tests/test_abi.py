@@ -111,3 +111,19 @@ def test_binding_refuses_missing_library(osb, tmp_path):
             m.load(str(tmp_path / "missing.so"))
     finally:
         m._lib = saved
+
+
+def test_noalloc_diagnostics_rejects_bad_arguments_before_gpu_work(osb):
+    """Argument checks of the allocation-free diagnostics run on the host,
+    before any CUDA call (fake, aligned, never-dereferenced pointers)."""
+    L = osb.load()
+    p = osb.Params(1600, 0.1, 1.4, 0.71, 1e-3)
+    ok_ptr = 4096
+    assert L.osb_diagnostics_noalloc(None, 8, 8, 8, 4, ctypes.byref(p), ok_ptr, None) == 1
+    assert L.osb_diagnostics_noalloc(ok_ptr, 8, 8, 8, 4, ctypes.byref(p), ok_ptr + 4, None) == 6
+    assert L.osb_diagnostics_noalloc(ok_ptr, 0, 8, 8, 4, ctypes.byref(p), ok_ptr, None) == 1
+    assert L.osb_diagnostics_noalloc(ok_ptr, 8, 8, 8, 5, ctypes.byref(p), ok_ptr, None) == 1
+    assert L.osb_diagnostics_noalloc(ok_ptr, 2048, 2048, 1024, 4, ctypes.byref(p), ok_ptr, None) == 1
+    assert b"too large" in L.osb_last_error()
+    bad = osb.Params(1600, 0.1, 1.0, 0.71, 1e-3)
+    assert L.osb_diagnostics_noalloc(ok_ptr, 8, 8, 8, 4, ctypes.byref(bad), ok_ptr, None) == 1
