@@ -48,6 +48,21 @@ cudaError_t launch_init_tgv(const Dims &d, const Phys &ph, double *U, size_t str
     return cudaGetLastError();
 }
 
+// FP32 copy of the FP64 accumulator (round to nearest), the stage-1 stencil
+// source of the FP32 path.
+__global__ void k_to_f32(const double *__restrict__ U, size_t us, float *__restrict__ q, size_t qs, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int m = 0; m < 5; ++m) q[m * qs + i] = d2f_bits(U[m * us + i]);
+}
+
+cudaError_t launch_to_f32(const double *U, size_t u_stride, float *q, size_t q_stride, int n, cudaStream_t st) {
+    int blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_to_f32<<<blocks, 256, 0, st>>>(U, u_stride, q, q_stride, n);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Diagnostics (Section 3.3): grid sums of (1/2) rho u_j u_j, (1/2) rho |omega|^2
 // with omega_i = eps_ijk D_j u_k, the conserved fields, the non-finite count

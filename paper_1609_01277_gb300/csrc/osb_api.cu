@@ -24,6 +24,8 @@ struct osb_grid {
     char *ws;
     cudaStream_t st;
     int cur;  // which FP64 accumulator holds Q^n
+    int qc;   // FP32 path: which stage register holds the FP32 copy of Q^n
+    int copy_valid;
     double t;
     long long step;
     double *U[2];
@@ -305,6 +307,7 @@ osb_status osb_init_taylor_green(osb_grid *g, const double *noise, double amp) {
     if (noise && !isfinite(amp)) return fail(OSB_ERR_INVALID_ARG, "noise amplitude not finite");
     cudaError_t e = launch_init_tgv(g->d, g->ph, g->U[g->cur], g->u_stride, noise, amp, g->st);
     if (e != cudaSuccess) return cuda_fail(e, "init_taylor_green");
+    g->copy_valid = 0;
     g->t = 0.0;
     g->step = 0;
     return OSB_OK;
@@ -329,6 +332,7 @@ static osb_status copy_state(osb_grid *g, const double *src, double *dst, cudaMe
         cudaError_t e = cudaStreamSynchronize(g->st);
         if (e != cudaSuccess) return cuda_fail(e, "state copy sync");
     }
+    if (dst == nullptr) g->copy_valid = 0;
     return OSB_OK;
 }
 
@@ -387,20 +391,38 @@ static osb_status rk3_one_step(osb_grid *g) {
     StageArgs a = base_args(g);
     double *Ucur = g->U[g->cur], *Unext = g->U[1 - g->cur];
     const double dt = g->prm.dt;
+    const bool f32 = g->desc.precision == OSB_FP32;
+    if (f32 && !g->copy_valid) {
+        cudaError_t e = launch_to_f32(Ucur, g->u_stride, (float *)g->q[g->qc], g->q_stride, g->d.n, g->st);
+        if (e != cudaSuccess) return cuda_fail(e, "fp32 copy launch");
+        g->copy_valid = 1;
+    }
+    // FP64: stage sources U_cur, q[0], q[1].  FP32: q[qc] (FP32 copy of U_cur),
+    // q[1-qc], q[qc]; the last stage writes the next copy into q[1-qc].
+    void *src[3], *qout[3];
+    if (f32) {
+        src[0] = g->q[g->qc];
+        src[1] = g->q[1 - g->qc];
+        src[2] = g->q[g->qc];
+        qout[0] = g->q[1 - g->qc];
+        qout[1] = g->q[g->qc];
+        qout[2] = nullptr;
+    } else {
+        src[0] = Ucur;
+        src[1] = g->q[0];
+        src[2] = g->q[1];
+        qout[0] = g->q[0];
+        qout[1] = g->q[1];
+        qout[2] = nullptr;
+    }
     for (int k = 0; k < 3; ++k) {
-        if (k == 0) {
-            a.src = Ucur;
-            a.src_is_f64 = 1;
-            a.src_stride = g->u_stride;
-            a.U_in = Ucur;
-        } else {
-            a.src = g->q[k - 1];
-            a.src_is_f64 = g->desc.precision == OSB_FP64;
-            a.src_stride = g->q_stride;
-            a.U_in = Unext;
-        }
+        a.src = src[k];
+        a.src_is_f64 = !f32;
+        a.src_stride = (k == 0 && !f32) ? g->u_stride : g->q_stride;
+        a.U_in = (k == 0) ? Ucur : Unext;
         a.U_out = Unext;
-        a.q_out = (k < 2) ? g->q[k] : nullptr;
+        a.q_out = qout[k];
+        a.u32_out = (f32 && k == 2) ? g->q[1 - g->qc] : nullptr;
         a.alpha_dt = RK_ALPHA[k] * dt;
         a.beta_dt = RK_BETA[k] * dt;
         a.ev = nullptr;
@@ -411,6 +433,7 @@ static osb_status rk3_one_step(osb_grid *g) {
         cudaError_t e = g->K.stage(a);
         if (e != cudaSuccess) return cuda_fail(e, "rk3 stage launch");
     }
+    if (f32) g->qc = 1 - g->qc;
     g->cur = 1 - g->cur;
     g->step += 1;
     g->t = g->step * dt;

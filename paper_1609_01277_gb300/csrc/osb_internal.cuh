@@ -77,6 +77,7 @@ struct StageArgs {
     void *q_out;            // next stage register (type T), or nullptr
     size_t u_stride, q_stride;
     double alpha_dt, beta_dt;
+    void *u32_out;          // FP32 path, last stage: FP32 copy of U_out (q_stride), or nullptr
     double *R_out;          // residual-only mode: FP64 residual (5 fields, R_stride)
     size_t R_stride;
     cudaStream_t stream;
@@ -112,5 +113,6 @@ cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const C
                                double dt, const double *U, size_t stride, double *partials,
                                int max_partials, double *result, cudaStream_t st);
 int diag_num_partials(const Dims &d);
+cudaError_t launch_to_f32(const double *U, size_t u_stride, float *q, size_t q_stride, int n, cudaStream_t st);
 
 }  // namespace osb

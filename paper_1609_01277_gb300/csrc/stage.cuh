@@ -99,6 +99,39 @@ __device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R> &nb, const
 
 constexpr int BX = 32, BY = 8;
 
+// Exact float -> double and round-to-nearest-even double -> float, on the
+// integer pipes (GB300 issues FP64 instructions, conversions included, at
+// 1/64 of the FP32 rate).  Values below the smallest normal float are flushed
+// to signed zero; infinities and NaNs are kept.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+    const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+    uint64_t r;
+    if (e == 0xffu)
+        r = sign | 0x7ff0000000000000ull | ((uint64_t)m << 29);
+    else if (e == 0u)
+        r = sign;
+    else
+        r = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+    return __longlong_as_double((long long)r);
+}
+
+__device__ __forceinline__ float d2f_bits(double d) {
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffu);
+    const uint64_t m = b & 0xfffffffffffffull;
+    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
+    const int fe = e - 1023 + 127;
+    if (fe >= 0xff) return __uint_as_float(sign | 0x7f800000u);
+    if (fe <= 0) return __uint_as_float(sign);
+    const uint32_t hi = (uint32_t)(m >> 29), lo = (uint32_t)(m & 0x1fffffffu);
+    uint32_t f = ((uint32_t)fe << 23) | hi;
+    if (lo > 0x10000000u || (lo == 0x10000000u && (hi & 1u))) f += 1u;  // carry into the exponent is correct
+    return __uint_as_float(sign | f);
+}
+
 // ---------------------------------------------------------------------------
 // k_prim: primitives and the point-wise momentum fluxes
 // ---------------------------------------------------------------------------
@@ -245,12 +278,28 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
 
     if (MODE == 0) {
         T *qo = static_cast<T *>(a.q_out);
+        if constexpr (sizeof(T) == 8) {
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const double Ui = a.U_in[m * a.u_stride + i];
-            const double Rm = double(res[m]);
-            a.U_out[m * a.u_stride + i] = fma(a.beta_dt, Rm, Ui);
-            if (qo) qo[m * a.q_stride + i] = T(fma(a.alpha_dt, Rm, Ui));
+            for (int m = 0; m < 5; ++m) {
+                const double Ui = a.U_in[m * a.u_stride + i];
+                const double Rm = double(res[m]);
+                a.U_out[m * a.u_stride + i] = fma(a.beta_dt, Rm, Ui);
+                if (qo) qo[m * a.q_stride + i] = T(fma(a.alpha_dt, Rm, Ui));
+            }
+        } else {
+            // FP32 path: the FP64 accumulator takes one DADD per field; the
+            // increment and the stage value are formed in FP32 and converted
+            // on the integer pipes.
+            float *cp = static_cast<float *>(a.u32_out);
+            const float bdt = float(a.beta_dt), adt = float(a.alpha_dt);
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const double Ui = a.U_in[m * a.u_stride + i];
+                const double Un = Ui + f2d_bits(bdt * float(res[m]));
+                a.U_out[m * a.u_stride + i] = Un;
+                if (qo) qo[m * a.q_stride + i] = T(fmaf(adt, float(res[m]), d2f_bits(Ui)));
+                if (cp) cp[m * a.q_stride + i] = d2f_bits(Un);
+            }
         }
     } else {
 #pragma unroll
