@@ -2,6 +2,7 @@
 // checks, buffer carving, the RK3 stage sequence and status codes.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <new>
@@ -26,6 +27,7 @@ struct osb_grid {
     int cur;  // which FP64 accumulator holds Q^n
     int qc;   // FP32 path: which stage register holds the FP32 copy of Q^n
     int copy_valid;
+    int zmarch;  // FP32 path kernels: 1 z-march (default), 0 three-kernel (OSB_FP32_STAGE=split3)
     double t;
     long long step;
     double *U[2];
@@ -134,6 +136,7 @@ StageArgs base_args(const osb_grid *g) {
     a.c32 = g->c32;
     a.precision = g->desc.precision;
     a.visc_form = g->desc.visc_form;
+    a.zmarch = g->zmarch;
     a.aux = g->aux;
     a.aux_stride = g->aux_stride;
     a.u_stride = g->u_stride;
@@ -241,6 +244,10 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     g->max_partials = diag_num_partials(g->d);
     g->result = g->partials + (size_t)g->max_partials * DIAG_STRIDE;
     g->cur = 0;
+    {
+        const char *env = getenv("OSB_FP32_STAGE");
+        g->zmarch = !(env && strcmp(env, "split3") == 0);
+    }
     *out = g;
     return OSB_OK;
 }

@@ -82,6 +82,7 @@ struct StageArgs {
     size_t R_stride;
     cudaStream_t stream;
     cudaEvent_t *ev;        // optional: 4 events recorded around the 3 kernels
+    int zmarch;             // FP32 path: 1 = z-marching two-kernel stage, 0 = three-kernel stage
 };
 
 // Kernel kinds reported by the profiling hooks.

@@ -1,4 +1,4 @@
 // stage_o2.cu -- stage kernels for central differences of order 2 (radius 1).
-#include "stage.cuh"
+#include "zmarch.cuh"
 
 OSB_DEFINE_ORDER(2)

@@ -1,4 +1,4 @@
 // stage_o8.cu -- stage kernels for central differences of order 8 (radius 4).
-#include "stage.cuh"
+#include "zmarch.cuh"
 
 OSB_DEFINE_ORDER(8)

@@ -1,0 +1,432 @@
+// zmarch.cuh -- FP32 stage as two z-marching kernels (orders 2..8, viscous
+// work form A), the memory-lean form of the three kernels in stage.cuh.
+//
+// Each CTA owns a TX x TY column tile of the grid and a chunk of z planes.
+// Planes stream through a shared-memory ring: plane L is copied with
+// cp.async (4-byte copies at wrapped addresses, so the periodic halo needs no
+// ghost cells) PF planes ahead of its use, over the tile plus an R-wide halo
+// in x and y.  Along z every thread keeps its own column in register queues of
+// 2R+1 values; x/y stencils read the ring, z stencils read the queues.
+//
+//   k_zflux: velocity gradient -> energy flux F_j (with the viscous work
+//            u_i tau_ij), g_i = div u - D_i u_i, div u          (7 FP32 fields)
+//   k_zrhs : residual of all equations + RK update, reading Q, F_j, g_i, div u
+//
+// HBM traffic per point and stage (FP32 q, FP64 U): k_zflux reads q (20 B)
+// and writes 28 B; k_zrhs reads q, F, g, div (48 B) and U (40 B), writes q
+// (20 B) and U (40 B), plus the 20 B FP32 copy of U in the last stage.
+#pragma once
+
+#include "stage.cuh"
+
+namespace osb {
+namespace zm {
+
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int PF = 2;  // planes in flight ahead of the lead plane
+
+template <int R>
+struct Geo {
+    static constexpr int RW = TX + 2 * R, RH = TY + 2 * R, RA = RW * RH;
+    static constexpr int NS = R + 1 + PF;  // ring slots
+};
+
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ int wrapz(int z, int nz) {
+    z %= nz;
+    return z < 0 ? z + nz : z;
+}
+
+// In-plane offsets of the tile rectangle (tile + R halo, periodic wrap).
+template <int R>
+__device__ __forceinline__ void make_offsets(int *off, int x0, int y0, const Dims &d) {
+    using G = Geo<R>;
+    for (int e = threadIdx.x; e < G::RA; e += NT) {
+        const int ry = e / G::RW, rx = e - ry * G::RW;
+        off[e] = wrapc(y0 + ry - R, d.ny) * d.nx + wrapc(x0 + rx - R, d.nx);
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void qpush(float (&q)[N], float v) {
+#pragma unroll
+    for (int k = 0; k < N - 1; ++k) q[k] = q[k + 1];
+    q[N - 1] = v;
+}
+
+// z derivatives from a register queue centred at index R.
+template <int R>
+__device__ __forceinline__ float qd1(const float (&q)[2 * R + 1], const float *c) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = R; k >= 1; --k) s = fmaf(c[k], q[R + k] - q[R - k], s);
+    return s;
+}
+template <int R>
+__device__ __forceinline__ float qd2(const float (&q)[2 * R + 1], const float *c) {
+    float s = c[0] * q[R];
+#pragma unroll
+    for (int k = R; k >= 1; --k) s = fmaf(c[k], q[R + k] + q[R - k], s);
+    return s;
+}
+// x / y derivatives from a shared-memory plane (rectangle layout).
+template <int R>
+__device__ __forceinline__ float sdx1(const float *p, int ce, const float *c) {
+    float s = 0.f;
+#pragma unroll
+    for (int k = R; k >= 1; --k) s = fmaf(c[k], p[ce + k] - p[ce - k], s);
+    return s;
+}
+template <int R>
+__device__ __forceinline__ float sdy1(const float *p, int ce, const float *c) {
+    constexpr int W = Geo<R>::RW;
+    float s = 0.f;
+#pragma unroll
+    for (int k = R; k >= 1; --k) s = fmaf(c[k], p[ce + k * W] - p[ce - k * W], s);
+    return s;
+}
+template <int R>
+__device__ __forceinline__ float sdx2(const float *p, int ce, const float *c) {
+    float s = c[0] * p[ce];
+#pragma unroll
+    for (int k = R; k >= 1; --k) s = fmaf(c[k], p[ce + k] + p[ce - k], s);
+    return s;
+}
+template <int R>
+__device__ __forceinline__ float sdy2(const float *p, int ce, const float *c) {
+    constexpr int W = Geo<R>::RW;
+    float s = c[0] * p[ce];
+#pragma unroll
+    for (int k = R; k >= 1; --k) s = fmaf(c[k], p[ce + k * W] + p[ce - k * W], s);
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// k_zflux
+// ---------------------------------------------------------------------------
+template <int R>
+struct FluxSmem {
+    using G = Geo<R>;
+    int off[G::RA];
+    float ring[G::NS][4][G::RA];  // rho, m0, m1, m2 over the rectangle
+    float ering[G::NS][NT];       // rho E at the tile points
+    float vel[3][G::RA];          // u_i of the output plane
+};
+
+template <int R>
+__global__ void __launch_bounds__(NT, 1) k_zflux(const StageArgs a, int zchunk) {
+    using G = Geo<R>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FluxSmem<R> &S = *reinterpret_cast<FluxSmem<R> *>(smem_raw);
+    const Dims d = a.d;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, d.nz);
+    const int ce = (ty + R) * G::RW + tx + R;
+    const bool active = (x0 + tx < d.nx) && (y0 + ty < d.ny);
+    const int plane = d.nx * d.ny;
+    const float *Q = static_cast<const float *>(a.src);
+    const size_t qs = a.src_stride, as = a.aux_stride;
+    float *aux = static_cast<float *>(a.aux);
+    const Coef<float> &c = a.c32;
+
+    make_offsets<R>(S.off, x0, y0, d);
+    __syncthreads();
+    const int coff = S.off[ce];
+
+    auto issue = [&](int L) {
+        const int s = ((L % G::NS) + G::NS) % G::NS;
+        const size_t zb = (size_t)wrapz(L, d.nz) * plane;
+        for (int e = tid; e < G::RA; e += NT) {
+            const size_t g = zb + S.off[e];
+#pragma unroll
+            for (int f = 0; f < 4; ++f) cp_async4(&S.ring[s][f][e], Q + f * qs + g);
+        }
+        cp_async4(&S.ering[s][tid], Q + 4 * qs + zb + coff);
+        cp_commit();
+    };
+
+    float qu[2 * R + 1], qv[2 * R + 1], qw[2 * R + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * R + 1; ++k) qu[k] = qv[k] = qw[k] = 0.f;
+
+    const int Lbeg = z0 - R, Lend = z1 + R;  // lead planes [Lbeg, Lend)
+#pragma unroll 1
+    for (int p = 0; p < PF; ++p) issue(Lbeg + p);
+    const float ir = float(a.ph.inv_re), gm1 = float(a.ph.gm1);
+#pragma unroll 1
+    for (int L = Lbeg; L < Lend; ++L) {
+        cp_wait<PF - 1>();
+        __syncthreads();
+        if (L + PF < Lend)
+            issue(L + PF);
+        else
+            cp_commit();  // keep the group count uniform
+        const int sL = ((L % G::NS) + G::NS) % G::NS;
+        {
+            const float rho = S.ring[sL][0][ce];
+            const float ri = 1.f / rho;
+            qpush(qu, S.ring[sL][1][ce] * ri);
+            qpush(qv, S.ring[sL][2][ce] * ri);
+            qpush(qw, S.ring[sL][3][ce] * ri);
+        }
+        const int zo = L - R;
+        if (zo < z0) continue;
+        const int so = ((zo % G::NS) + G::NS) % G::NS;
+        for (int e = tid; e < G::RA; e += NT) {
+            const float ri = 1.f / S.ring[so][0][e];
+            S.vel[0][e] = S.ring[so][1][e] * ri;
+            S.vel[1][e] = S.ring[so][2][e] * ri;
+            S.vel[2][e] = S.ring[so][3][e] * ri;
+        }
+        __syncthreads();
+        const float gxx = sdx1<R>(S.vel[0], ce, c.d1[0]), gxy = sdy1<R>(S.vel[0], ce, c.d1[1]),
+                    gxz = qd1<R>(qu, c.d1[2]);
+        const float gyx = sdx1<R>(S.vel[1], ce, c.d1[0]), gyy = sdy1<R>(S.vel[1], ce, c.d1[1]),
+                    gyz = qd1<R>(qv, c.d1[2]);
+        const float gzx = sdx1<R>(S.vel[2], ce, c.d1[0]), gzy = sdy1<R>(S.vel[2], ce, c.d1[1]),
+                    gzz = qd1<R>(qw, c.d1[2]);
+        const float div = gxx + gyy + gzz;
+        const float tdiv = (2.f / 3.f) * div;
+        const float txx = ir * (gxx + gxx - tdiv), tyy = ir * (gyy + gyy - tdiv), tzz = ir * (gzz + gzz - tdiv);
+        const float txy = ir * (gxy + gyx), txz = ir * (gxz + gzx), tyz = ir * (gyz + gzy);
+        const float u = qu[R], v = qv[R], w = qw[R];
+        const float rho = S.ring[so][0][ce], e = S.ering[so][tid];
+        const float p = gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
+        const float hE = fmaf(0.5f, e, p);
+        if (active) {
+            const size_t i = (size_t)zo * plane + coff;
+            aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
+            aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
+            aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
+            aux[A_GX * as + i] = gyy + gzz;
+            aux[A_GY * as + i] = gxx + gzz;
+            aux[A_GZ * as + i] = gxx + gyy;
+            aux[A_DIV * as + i] = div;
+        }
+    }
+    cp_wait<0>();
+}
+
+// ---------------------------------------------------------------------------
+// k_zrhs
+// ---------------------------------------------------------------------------
+enum RingField { RF_RHO = 0, RF_M0, RF_M1, RF_M2, RF_E, RF_FX, RF_FY, RF_GX, RF_GY, RF_N };
+enum DerField { DF_U = 0, DF_V, DF_W, DF_T, DF_PXX, DF_PYY, DF_PXY, DF_PXZ, DF_PYZ, DF_N };
+
+template <int R>
+struct RhsSmem {
+    using G = Geo<R>;
+    int off[G::RA];
+    float ring[G::NS][RF_N][G::RA];
+    float cring[G::NS][2][NT];  // F_z, g_z at the tile points
+    float der[DF_N][G::RA];
+};
+
+template <int R>
+__global__ void __launch_bounds__(NT, 1) k_zrhs(const StageArgs a, int zchunk) {
+    using G = Geo<R>;
+    constexpr int Q = 2 * R + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    RhsSmem<R> &S = *reinterpret_cast<RhsSmem<R> *>(smem_raw);
+    const Dims d = a.d;
+    const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, d.nz);
+    const int ce = (ty + R) * G::RW + tx + R;
+    const bool active = (x0 + tx < d.nx) && (y0 + ty < d.ny);
+    const int plane = d.nx * d.ny;
+    const float *Qg = static_cast<const float *>(a.src);
+    const size_t qs = a.src_stride, as = a.aux_stride;
+    const float *aux = static_cast<const float *>(a.aux);
+    const Coef<float> &c = a.c32;
+
+    make_offsets<R>(S.off, x0, y0, d);
+    __syncthreads();
+    const int coff = S.off[ce];
+
+    auto issue = [&](int L) {
+        const int s = ((L % G::NS) + G::NS) % G::NS;
+        const size_t zb = (size_t)wrapz(L, d.nz) * plane;
+        const float *src[RF_N] = {Qg, Qg + qs, Qg + 2 * qs, Qg + 3 * qs, Qg + 4 * qs,
+                                  aux + A_FX * as, aux + A_FY * as, aux + A_GX * as, aux + A_GY * as};
+        for (int e = tid; e < G::RA; e += NT) {
+            const size_t g = zb + S.off[e];
+#pragma unroll
+            for (int f = 0; f < RF_N; ++f) cp_async4(&S.ring[s][f][e], src[f] + g);
+        }
+        cp_async4(&S.cring[s][0][tid], aux + A_FZ * as + zb + coff);
+        cp_async4(&S.cring[s][1][tid], aux + A_GZ * as + zb + coff);
+        cp_commit();
+    };
+
+    // register queues along z (planes zo-R .. zo+R once full)
+    float qQ[5][Q], qPxz[Q], qPyz[Q], qPzz[Q], qFz[Q], qU[Q], qV[Q], qW[Q], qT[Q];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) qQ[m][k] = 0.f;
+        qPxz[k] = qPyz[k] = qPzz[k] = qFz[k] = qU[k] = qV[k] = qW[k] = qT[k] = 0.f;
+    }
+    const float ir = float(a.ph.inv_re), ir3 = ir * (1.f / 3.f), gm1 = float(a.ph.gm1),
+                gM2 = float(a.ph.gM2), kap = float(a.ph.kappa), f43 = 4.f / 3.f;
+    const float bdt = float(a.beta_dt), adt = float(a.alpha_dt);
+    float *qo = static_cast<float *>(a.q_out);
+    float *cp = static_cast<float *>(a.u32_out);
+
+    const int Lbeg = z0 - R, Lend = z1 + R;
+#pragma unroll 1
+    for (int p = 0; p < PF; ++p) issue(Lbeg + p);
+#pragma unroll 1
+    for (int L = Lbeg; L < Lend; ++L) {
+        cp_wait<PF - 1>();
+        __syncthreads();
+        if (L + PF < Lend)
+            issue(L + PF);
+        else
+            cp_commit();
+        const int sL = ((L % G::NS) + G::NS) % G::NS;
+        {   // lead plane: point-wise quantities of this thread's column
+            const float rho = S.ring[sL][RF_RHO][ce], m0 = S.ring[sL][RF_M0][ce], m1 = S.ring[sL][RF_M1][ce],
+                        m2 = S.ring[sL][RF_M2][ce], e = S.ring[sL][RF_E][ce];
+            const float ri = 1.f / rho;
+            const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
+            const float p = gm1 * (e - 0.5f * (m0 * u + m1 * v + m2 * w));
+            qpush(qQ[0], rho);
+            qpush(qQ[1], m0);
+            qpush(qQ[2], m1);
+            qpush(qQ[3], m2);
+            qpush(qQ[4], e);
+            qpush(qU, u);
+            qpush(qV, v);
+            qpush(qW, w);
+            qpush(qT, gM2 * p * ri);
+            qpush(qPxz, 0.5f * m0 * w);
+            qpush(qPyz, 0.5f * m1 * w);
+            qpush(qPzz, fmaf(0.5f * m2, w, p) - ir3 * S.cring[sL][1][tid]);
+            qpush(qFz, S.cring[sL][0][tid]);
+        }
+        const int zo = L - R;
+        if (zo < z0) continue;
+        const int so = ((zo % G::NS) + G::NS) % G::NS;
+        const size_t i = (size_t)zo * plane + coff;
+        // FP64 accumulator of this point: issue the loads before the plane work
+        double Ui[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) Ui[m] = a.U_in[m * a.u_stride + i];
+        const float divc = aux[A_DIV * as + i];
+        // point-wise fields of the output plane over the rectangle
+        for (int e = tid; e < G::RA; e += NT) {
+            const float rho = S.ring[so][RF_RHO][e], m0 = S.ring[so][RF_M0][e], m1 = S.ring[so][RF_M1][e],
+                        m2 = S.ring[so][RF_M2][e], en = S.ring[so][RF_E][e];
+            const float ri = 1.f / rho;
+            const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
+            const float p = gm1 * (en - 0.5f * (m0 * u + m1 * v + m2 * w));
+            S.der[DF_U][e] = u;
+            S.der[DF_V][e] = v;
+            S.der[DF_W][e] = w;
+            S.der[DF_T][e] = gM2 * p * ri;
+            S.der[DF_PXX][e] = fmaf(0.5f * m0, u, p) - ir3 * S.ring[so][RF_GX][e];
+            S.der[DF_PYY][e] = fmaf(0.5f * m1, v, p) - ir3 * S.ring[so][RF_GY][e];
+            S.der[DF_PXY][e] = 0.5f * m0 * v;
+            S.der[DF_PXZ][e] = 0.5f * m0 * w;
+            S.der[DF_PYZ][e] = 0.5f * m1 * w;
+        }
+        __syncthreads();
+        const float u = qU[R], v = qV[R], w = qW[R];
+        float res[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            const float *f = S.ring[so][RF_RHO + m];
+            const float dx = sdx1<R>(f, ce, c.d1[0]), dy = sdy1<R>(f, ce, c.d1[1]), dz = qd1<R>(qQ[m], c.d1[2]);
+            res[m] = -0.5f * fmaf(u, dx, fmaf(v, dy, fmaf(w, dz, qQ[m][R] * divc)));
+            if (m == 1) res[0] = fmaf(-0.5f, dx, res[0]);
+            if (m == 2) res[0] = fmaf(-0.5f, dy, res[0]);
+            if (m == 3) res[0] = fmaf(-0.5f, dz, res[0]);
+        }
+        res[1] -= sdx1<R>(S.der[DF_PXX], ce, c.d1[0]) + sdy1<R>(S.der[DF_PXY], ce, c.d1[1]) + qd1<R>(qPxz, c.d1[2]);
+        res[2] -= sdx1<R>(S.der[DF_PXY], ce, c.d1[0]) + sdy1<R>(S.der[DF_PYY], ce, c.d1[1]) + qd1<R>(qPyz, c.d1[2]);
+        res[3] -= sdx1<R>(S.der[DF_PXZ], ce, c.d1[0]) + sdy1<R>(S.der[DF_PYZ], ce, c.d1[1]) + qd1<R>(qPzz, c.d1[2]);
+        res[4] -= sdx1<R>(S.ring[so][RF_FX], ce, c.d1[0]) + sdy1<R>(S.ring[so][RF_FY], ce, c.d1[1]) +
+                  qd1<R>(qFz, c.d1[2]);
+        res[1] += ir * fmaf(f43, sdx2<R>(S.der[DF_U], ce, c.d2[0]),
+                            sdy2<R>(S.der[DF_U], ce, c.d2[1]) + qd2<R>(qU, c.d2[2]));
+        res[2] += ir * fmaf(f43, sdy2<R>(S.der[DF_V], ce, c.d2[1]),
+                            sdx2<R>(S.der[DF_V], ce, c.d2[0]) + qd2<R>(qV, c.d2[2]));
+        res[3] += ir * fmaf(f43, qd2<R>(qW, c.d2[2]),
+                            sdx2<R>(S.der[DF_W], ce, c.d2[0]) + sdy2<R>(S.der[DF_W], ce, c.d2[1]));
+        res[4] = fmaf(kap, sdx2<R>(S.der[DF_T], ce, c.d2[0]) + sdy2<R>(S.der[DF_T], ce, c.d2[1]) +
+                               qd2<R>(qT, c.d2[2]), res[4]);
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const double Un = Ui[m] + f2d_bits(bdt * res[m]);
+                a.U_out[m * a.u_stride + i] = Un;
+                if (qo) qo[m * a.q_stride + i] = fmaf(adt, res[m], d2f_bits(Ui[m]));
+                if (cp) cp[m * a.q_stride + i] = d2f_bits(Un);
+            }
+        }
+    }
+    cp_wait<0>();
+}
+
+template <int R>
+constexpr size_t flux_smem() {
+    return sizeof(FluxSmem<R>);
+}
+template <int R>
+constexpr size_t rhs_smem() {
+    return sizeof(RhsSmem<R>);
+}
+
+// Launches k_zflux then k_zrhs for one RK stage of the FP32 path.
+template <int R>
+cudaError_t launch_zstage(const StageArgs &a) {
+    static_assert(R <= 4, "z-march kernels are built for orders up to 8");
+    const int zchunk = 32;
+    dim3 grd((a.d.nx + TX - 1) / TX, (a.d.ny + TY - 1) / TY, (a.d.nz + zchunk - 1) / zchunk);
+    const size_t sf = flux_smem<R>(), sr = rhs_smem<R>();
+    cudaError_t e = cudaFuncSetAttribute(k_zflux<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_zrhs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
+    if (e != cudaSuccess) return e;
+    if (a.ev) cudaEventRecord(a.ev[0], a.stream);
+    if (a.ev) cudaEventRecord(a.ev[1], a.stream);  // no separate primitive kernel
+    k_zflux<R><<<grd, NT, sf, a.stream>>>(a, zchunk);
+    if (a.ev) cudaEventRecord(a.ev[2], a.stream);
+    k_zrhs<R><<<grd, NT, sr, a.stream>>>(a, zchunk);
+    if (a.ev) cudaEventRecord(a.ev[3], a.stream);
+    return cudaGetLastError();
+}
+
+}  // namespace zm
+
+// Per-order stage entry: the z-march kernels for the FP32 path (form A,
+// orders <= 8), the three-kernel stage otherwise.
+template <int R>
+cudaError_t stage_entry_z(const StageArgs &a) {
+    if constexpr (R <= 4) {
+        if (a.precision == OSB_FP32 && a.visc_form == OSB_VISC_A && !a.src_is_f64 && a.zmarch)
+            return zm::launch_zstage<R>(a);
+    }
+    return launch_stage<R>(a, 0);
+}
+
+}  // namespace osb
+
+#undef OSB_DEFINE_ORDER
+#define OSB_DEFINE_ORDER(ORDER)                                                          \
+    namespace osb {                                                                      \
+    OrderKernels kernels_o##ORDER() {                                                    \
+        return OrderKernels{ORDER, &stage_entry_z<ORDER / 2>, &residual_entry<ORDER / 2>}; \
+    }                                                                                    \
+    }

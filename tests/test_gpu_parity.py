@@ -274,3 +274,49 @@ def test_fp32_tgv_steps_close_to_oracle(osb):
         scale = mnorm if 1 <= m <= 3 else np.linalg.norm(Qo[m].ravel())
         err = np.linalg.norm((Q[m] - Qo[m]).ravel()) / scale
         assert err < 1e-5, (m, err)
+
+
+def _fp32_err(Q, Qo):
+    """Per-field error of an FP32-path state: momentum components against the
+    momentum magnitude, the others against their own norm."""
+    mnorm = np.linalg.norm(Qo[1:4].ravel())
+    out = []
+    for m in range(5):
+        scale = mnorm if 1 <= m <= 3 else np.linalg.norm(Qo[m].ravel())
+        out.append(np.linalg.norm((Q[m] - Qo[m]).ravel()) / scale)
+    return out
+
+
+@pytest.mark.parametrize("dims,order", [((32, 32, 32), 4), ((40, 24, 48), 8), ((8, 8, 8), 8),
+                                        ((37, 20, 9), 2), ((24, 16, 40), 6), ((70, 9, 33), 4)])
+def test_fp32_zmarch_steps_close_to_oracle(osb, dims, order):
+    """The z-marching FP32 stage (tiles of 32x8 columns, 32-plane z chunks,
+    ragged tiles, nz below the stencil width) against the FP64 oracle, with
+    the FP32 bound derived in test_fp32_tgv_steps_close_to_oracle."""
+    nx, ny, nz = dims
+    steps = 10
+    noise = inputs.gaussian_noise(nx, ny, nz, seed=77)
+    g = _grid(osb, nx, ny, nz, order=order, precision=osb.OSB_FP32, dt=2e-3, Re=200.0)
+    g.init_taylor_green(noise, 1e-2)
+    g.step(steps)
+    case = _case(nx, ny, nz, order=order, dt=2e-3, Re=200.0)
+    Qo = orc.rk3_step(case, orc.tgv_init(case, noise, 1e-2), steps)
+    for m, err in enumerate(_fp32_err(g.get_state(), Qo)):
+        assert err < 1e-5, (m, err)
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_fp32_zmarch_agrees_with_three_kernel_stage(osb, order, monkeypatch):
+    """The two FP32 stage implementations evaluate the same discrete operator:
+    their states after 5 steps differ only by FP32 rounding."""
+    n = 40
+    noise = inputs.gaussian_noise(n, n, n, seed=5)
+    out = []
+    for mode in ("zmarch", "split3"):
+        monkeypatch.setenv("OSB_FP32_STAGE", mode)
+        g = _grid(osb, n, n, n, order=order, precision=osb.OSB_FP32)
+        g.init_taylor_green(noise, 1e-3)
+        g.step(5)
+        out.append(g.get_state())
+    for m, err in enumerate(_fp32_err(out[0], out[1])):
+        assert err < 2e-6, (m, err)
