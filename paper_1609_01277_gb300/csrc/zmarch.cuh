@@ -123,7 +123,7 @@ struct FluxSmem {
 };
 
 template <int R>
-__global__ void __launch_bounds__(NT, 1) k_zflux(const StageArgs a, int zchunk) {
+__global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk) {
     using G = Geo<R>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     FluxSmem<R> &S = *reinterpret_cast<FluxSmem<R> *>(smem_raw);
@@ -233,7 +233,7 @@ struct RhsSmem {
 };
 
 template <int R>
-__global__ void __launch_bounds__(NT, 1) k_zrhs(const StageArgs a, int zchunk) {
+__global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a, int zchunk) {
     using G = Geo<R>;
     constexpr int Q = 2 * R + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
