@@ -146,10 +146,37 @@ osb_status osb_rk3_step(osb_grid *grid, int nsteps);
  * OSB_ERR_NONFINITE (with *out filled) if any conserved value is NaN/Inf. */
 osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
 
-/* Advances n independent grids (an ensemble of uneven sizes and parameters)
- * by nsteps steps each.  All grids must share one stream.  OSB_ERR_TIMEOUT if
- * a bounded device-side wait gave up. */
+/* Advances n independent grids (an ensemble of uneven sizes, Reynolds and
+ * Mach numbers and time steps; spec extension of the paper's Section
+ * 3.3 solver) by nsteps RK3 steps each, in ONE persistent kernel launch that
+ * is captured into a CUDA graph on first use and replayed on later calls with
+ * the same grids, parities and nsteps.  Work items (step, stage phase,
+ * instance, tile) are taken in order by resident CTAs; a per-instance
+ * completion count orders the phases of each instance.  Each tile is 32 x 8
+ * points by tz planes, tz chosen per grid shape by osb_autotune (default 4).
+ * Requirements: 1 <= n <= 128 distinct grids on one stream with the same
+ * order, precision and viscous form (else OSB_ERR_INVALID_ARG /
+ * OSB_ERR_UNSUPPORTED).  Synchronises the stream (it reads the status word).
+ * OSB_ERR_TIMEOUT: a device-side wait exceeded its limit (osb_batch_configure);
+ * the kernel stopped and the grids' states are undefined, the CUDA context
+ * stays usable.  Results equal those of osb_rk3_step on each grid. */
 osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps);
+
+/* Ensemble controls (tooling; no counterpart in the paper).  wait_limit_seconds
+ * bounds every per-instance wait of osb_batch_step (default 2 s; must be in
+ * (0, 3600]).  test_stall != 0 makes the first wait of the next batches target
+ * a count that nothing reaches, so the wait runs out and the call returns
+ * OSB_ERR_TIMEOUT -- used to test the failure path without faulting a GPU.
+ * Process-wide settings. */
+osb_status osb_batch_configure(double wait_limit_seconds, int test_stall);
+
+/* Times osb_batch_step on this grid alone for each candidate tile depth
+ * (1, 2, 4, 8, 16 z planes), trial_steps steps each, and keeps the fastest for
+ * the grid's shape (nx, ny, nz, order, precision, form) in a process-wide table,
+ * also written to the file named by $OSB_AUTOTUNE_CACHE when set (read back
+ * on first use).  The grid's state, time and step count are restored
+ * afterwards (through a host copy).  *best_tz receives the choice (may be NULL). */
+osb_status osb_autotune(osb_grid *grid, int trial_steps, int *best_tz);
 
 /* Diagnostics of a caller-provided state without any device allocation and
  * without a grid object.  The paper has no counterpart: this entry point exists

@@ -1,0 +1,144 @@
+// batch.cu -- an ensemble of independent periodic grids (uneven sizes and
+// parameters) advanced by ONE persistent kernel launch for many RK3 steps.
+//
+// Work items are (step, phase, instance, tile), phase = 3 RK stages x 3
+// sub-steps (primitives, gradient fluxes, residual + update).  CTAs take items
+// in order from a global counter.  Each instance keeps a count of its
+// completed items; an item of sequence s = 9*step + phase of instance i starts
+// only when that count reaches s * tiles_i, i.e. when every item of the
+// instance's previous phases is done (a per-instance barrier).  Waits only ever
+// target items that running CTAs took earlier, so the scheme cannot deadlock;
+// each wait is still bounded by a time limit (%globaltimer), after which the
+// kernel raises an error flag that every CTA observes and exits.  While one
+// instance waits, CTAs keep taking items of the others: small and large grids
+// share the GPU without per-instance launches.
+//
+// Intermediate data written by other CTAs during the launch is read through
+// L2 (ld.global.cg), never through the non-coherent per-SM L1.
+#include "stage.cuh"
+
+namespace osb {
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int *p) {
+    int v;
+    asm volatile("ld.volatile.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <typename T, int R, bool VB>
+__global__ void __launch_bounds__(BX *BY) k_batch(const BatchParams P) {
+    __shared__ StageArgs sa;
+    __shared__ long long item_s;
+    __shared__ int stop_s;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    while (true) {
+        if (tid == 0) {
+            item_s = (long long)atomicAdd(P.counter, 1ull);
+            stop_s = ld_volatile_i32(P.err) != 0;
+        }
+        __syncthreads();
+        const long long k = item_s;
+        if (k >= P.total_items || stop_s) break;
+        const long long seq = k / P.tiles_total;
+        const int rem = (int)(k - seq * P.tiles_total);
+        int inst = 0;
+        while (rem >= P.prefix[inst + 1]) ++inst;
+        const int tile = rem - P.prefix[inst];
+        const int tiles_i = P.prefix[inst + 1] - P.prefix[inst];
+        const BatchInst *B = P.rec[inst];
+        const int step = (int)(seq / 9), phase = (int)(seq % 9), stage = phase / 3, sub = phase % 3;
+        if (tid == 0) {
+            const unsigned target = P.inject_stall ? 0xffffffffu : (unsigned)(seq * tiles_i);
+            if (ld_acquire_u32(P.done + inst) < target) {
+                const unsigned long long t0 = globaltimer();
+                while (true) {
+                    if (ld_volatile_i32(P.err)) {
+                        stop_s = 1;
+                        break;
+                    }
+                    if (ld_acquire_u32(P.done + inst) >= target) break;
+                    if (globaltimer() - t0 > (unsigned long long)P.timeout_ns) {
+                        atomicExch(P.err, 1);
+                        stop_s = 1;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+        }
+        // stage arguments of this instance and step parity into shared memory
+        {
+            const int par = (P.p0[inst] + step) & 1;
+            const int *src = reinterpret_cast<const int *>(&B->st[par][stage]);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int w = tid; w < (int)(sizeof(StageArgs) / sizeof(int)); w += BX * BY) dst[w] = src[w];
+        }
+        __syncthreads();
+        if (stop_s) break;
+        const int txi = tile % B->tiles_x, tyi = (tile / B->tiles_x) % B->tiles_y, tzi = tile / (B->tiles_x * B->tiles_y);
+        const int x = txi * BX + threadIdx.x, y = tyi * BY + threadIdx.y;
+        const int zb = tzi * B->tz, ze = min(zb + B->tz, sa.d.nz);
+        if (x < sa.d.nx && y < sa.d.ny) {
+            for (int z = zb; z < ze; ++z) {
+                if (sub == 0)
+                    prim_point<LD_CG, T, T>(sa, x, y, z);
+                else if (sub == 1)
+                    grad_point<LD_CG, T, T, R, VB>(sa, x, y, z);
+                else
+                    resid_point<LD_CG, T, T, R, 0, VB>(sa, x, y, z);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(P.done + inst, 1u);
+        }
+    }
+}
+
+template <typename T, int R, bool VB>
+static cudaError_t launch_batch_t(const BatchParams &P, cudaStream_t st) {
+    int per_sm = 0, sms = 0, dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<T, R, VB>, BX * BY, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = (long long)per_sm * sms;
+    if (blocks > P.total_items) blocks = P.total_items > 0 ? P.total_items : 1;
+    k_batch<T, R, VB><<<(unsigned)blocks, dim3(BX, BY, 1), 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <int R>
+static cudaError_t launch_batch_r(const BatchParams &P, int precision, int visc_form, cudaStream_t st) {
+    if (precision == OSB_FP64)
+        return visc_form == OSB_VISC_B ? launch_batch_t<double, R, true>(P, st) : launch_batch_t<double, R, false>(P, st);
+    return visc_form == OSB_VISC_B ? launch_batch_t<float, R, true>(P, st) : launch_batch_t<float, R, false>(P, st);
+}
+
+cudaError_t launch_batch(const BatchParams &P, int order, int precision, int visc_form, cudaStream_t st) {
+    switch (order / 2) {
+        case 1: return launch_batch_r<1>(P, precision, visc_form, st);
+        case 2: return launch_batch_r<2>(P, precision, visc_form, st);
+        case 3: return launch_batch_r<3>(P, precision, visc_form, st);
+        case 4: return launch_batch_r<4>(P, precision, visc_form, st);
+        case 5: return launch_batch_r<5>(P, precision, visc_form, st);
+        case 6: return launch_batch_r<6>(P, precision, visc_form, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace osb

@@ -5,6 +5,8 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -41,6 +43,12 @@ struct osb_grid {
     // profiling: 4 events per stage launch, recorded on the grid's stream
     std::vector<cudaEvent_t> *prof_ev;
     int prof_used, prof_cap;
+    // ensemble stepping: this grid's device record and, when it leads a
+    // batch, the batch counters and the cache of captured CUDA graphs
+    BatchInst *batch_rec;
+    char *batch_ctl;
+    std::map<std::string, cudaGraphExec_t> *graphs;
+    cudaStream_t capture_st;  // library-owned stream the batch graphs are captured on
 };
 
 namespace {
@@ -54,6 +62,7 @@ osb_status fail(osb_status s, const char *msg) {
 
 osb_status cuda_fail(cudaError_t e, const char *where) {
     g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    (void)cudaGetLastError();  // do not leave a non-sticky error for the next launch check
     return OSB_ERR_CUDA;
 }
 
@@ -81,6 +90,11 @@ size_t state_bytes(const osb_grid_desc *d) {
 }
 
 size_t aux_bytes(const osb_grid_desc *d) { return NAUX * field_bytes(npoints(d), tsize(d)); }
+
+// Per-grid ensemble block: the device record (stage arguments for both step
+// parities), then the batch counters used when this grid leads a batch.
+constexpr size_t BATCH_CTL_BYTES = 1024;  // counter (8 B), error word, done[MAXB]
+size_t batch_bytes() { return round256(sizeof(BatchInst)) + BATCH_CTL_BYTES; }
 
 size_t diag_bytes(const osb_grid_desc *d) {
     Dims dd{d->nx, d->ny, d->nz, (int)npoints(d)};
@@ -200,7 +214,9 @@ const char *osb_last_error(void) { return g_err.c_str(); }
 
 size_t osb_state_bytes(const osb_grid_desc *d) { return desc_ok(d) ? state_bytes(d) : 0; }
 
-size_t osb_workspace_bytes(const osb_grid_desc *d) { return desc_ok(d) ? aux_bytes(d) + diag_bytes(d) : 0; }
+size_t osb_workspace_bytes(const osb_grid_desc *d) {
+    return desc_ok(d) ? aux_bytes(d) + diag_bytes(d) + batch_bytes() : 0;
+}
 
 osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, void *state_dev, size_t state_len,
                            void *ws_dev, size_t ws_len, void *stream, osb_grid **out) {
@@ -215,7 +231,7 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     if (((uintptr_t)state_dev & 255) || ((uintptr_t)ws_dev & 255))
         return fail(OSB_ERR_BUFFER, "device buffers must be 256-byte aligned");
     if (state_len < state_bytes(desc)) return fail(OSB_ERR_BUFFER, "state buffer too small");
-    if (ws_len < aux_bytes(desc) + diag_bytes(desc)) return fail(OSB_ERR_BUFFER, "workspace too small");
+    if (ws_len < aux_bytes(desc) + diag_bytes(desc) + batch_bytes()) return fail(OSB_ERR_BUFFER, "workspace too small");
 
     osb_grid *g = new (std::nothrow) osb_grid;
     if (!g) return fail(OSB_ERR_INVALID_ARG, "host allocation failed");
@@ -243,6 +259,8 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     g->partials = (double *)(g->ws + NAUX * fT);
     g->max_partials = diag_num_partials(g->d);
     g->result = g->partials + (size_t)g->max_partials * DIAG_STRIDE;
+    g->batch_rec = (BatchInst *)(g->ws + aux_bytes(desc) + diag_bytes(desc));
+    g->batch_ctl = (char *)g->batch_rec + round256(sizeof(BatchInst));
     g->cur = 0;
     {
         const char *env = getenv("OSB_FP32_STAGE");
@@ -263,6 +281,11 @@ static void prof_free(osb_grid *g) {
 osb_status osb_grid_destroy(osb_grid *g) {
     if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
     prof_free(g);
+    if (g->graphs) {
+        for (auto &kv : *g->graphs) cudaGraphExecDestroy(kv.second);
+        delete g->graphs;
+    }
+    if (g->capture_st) cudaStreamDestroy(g->capture_st);
     delete g;
     return OSB_OK;
 }
@@ -394,45 +417,55 @@ osb_status osb_residual(osb_grid *g, double *R_dev) {
 static const double RK_ALPHA[3] = {2.0 / 3.0, 5.0 / 12.0, 3.0 / 5.0};
 static const double RK_BETA[3] = {1.0 / 4.0, 3.0 / 20.0, 3.0 / 5.0};
 
-static osb_status rk3_one_step(osb_grid *g) {
+// Stage k (0..2) of a step that starts with Q^n in U[cur].  FP64: stencil
+// sources U[cur], q[0], q[1].  FP32: q[qc] (FP32 copy of U[cur]), q[1-qc],
+// q[qc], and the last stage writes the next copy into q[1-qc]; qc == cur.
+static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     StageArgs a = base_args(g);
-    double *Ucur = g->U[g->cur], *Unext = g->U[1 - g->cur];
-    const double dt = g->prm.dt;
     const bool f32 = g->desc.precision == OSB_FP32;
-    if (f32 && !g->copy_valid) {
-        cudaError_t e = launch_to_f32(Ucur, g->u_stride, (float *)g->q[g->qc], g->q_stride, g->d.n, g->st);
-        if (e != cudaSuccess) return cuda_fail(e, "fp32 copy launch");
-        g->copy_valid = 1;
-    }
-    // FP64: stage sources U_cur, q[0], q[1].  FP32: q[qc] (FP32 copy of U_cur),
-    // q[1-qc], q[qc]; the last stage writes the next copy into q[1-qc].
+    const int qc = cur;
+    double *Ucur = g->U[cur], *Unext = g->U[1 - cur];
     void *src[3], *qout[3];
     if (f32) {
-        src[0] = g->q[g->qc];
-        src[1] = g->q[1 - g->qc];
-        src[2] = g->q[g->qc];
-        qout[0] = g->q[1 - g->qc];
-        qout[1] = g->q[g->qc];
-        qout[2] = nullptr;
+        src[0] = g->q[qc];
+        src[1] = g->q[1 - qc];
+        src[2] = g->q[qc];
+        qout[0] = g->q[1 - qc];
+        qout[1] = g->q[qc];
     } else {
         src[0] = Ucur;
         src[1] = g->q[0];
         src[2] = g->q[1];
         qout[0] = g->q[0];
         qout[1] = g->q[1];
-        qout[2] = nullptr;
     }
+    qout[2] = nullptr;
+    a.src = src[k];
+    a.src_is_f64 = !f32;
+    a.src_stride = (k == 0 && !f32) ? g->u_stride : g->q_stride;
+    a.U_in = (k == 0) ? Ucur : Unext;
+    a.U_out = Unext;
+    a.q_out = qout[k];
+    a.u32_out = (f32 && k == 2) ? g->q[1 - qc] : nullptr;
+    a.alpha_dt = RK_ALPHA[k] * g->prm.dt;
+    a.beta_dt = RK_BETA[k] * g->prm.dt;
+    a.ev = nullptr;
+    return a;
+}
+
+static osb_status ensure_f32_copy(osb_grid *g) {
+    if (g->desc.precision != OSB_FP32 || g->copy_valid) return OSB_OK;
+    cudaError_t e = launch_to_f32(g->U[g->cur], g->u_stride, (float *)g->q[g->cur], g->q_stride, g->d.n, g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "fp32 copy launch");
+    g->copy_valid = 1;
+    return OSB_OK;
+}
+
+static osb_status rk3_one_step(osb_grid *g) {
+    osb_status s0 = ensure_f32_copy(g);
+    if (s0 != OSB_OK) return s0;
     for (int k = 0; k < 3; ++k) {
-        a.src = src[k];
-        a.src_is_f64 = !f32;
-        a.src_stride = (k == 0 && !f32) ? g->u_stride : g->q_stride;
-        a.U_in = (k == 0) ? Ucur : Unext;
-        a.U_out = Unext;
-        a.q_out = qout[k];
-        a.u32_out = (f32 && k == 2) ? g->q[1 - g->qc] : nullptr;
-        a.alpha_dt = RK_ALPHA[k] * dt;
-        a.beta_dt = RK_BETA[k] * dt;
-        a.ev = nullptr;
+        StageArgs a = stage_args(g, g->cur, k);
         if (g->prof_ev && g->prof_used < g->prof_cap) {
             a.ev = g->prof_ev->data() + 4 * g->prof_used;
             g->prof_used += 1;
@@ -440,10 +473,10 @@ static osb_status rk3_one_step(osb_grid *g) {
         cudaError_t e = g->K.stage(a);
         if (e != cudaSuccess) return cuda_fail(e, "rk3 stage launch");
     }
-    if (f32) g->qc = 1 - g->qc;
     g->cur = 1 - g->cur;
+    g->qc = g->cur;
     g->step += 1;
-    g->t = g->step * dt;
+    g->t = g->step * g->prm.dt;
     return OSB_OK;
 }
 
@@ -477,17 +510,249 @@ osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
     return OSB_OK;
 }
 
-osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) {
-    if (!grids || n < 0 || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Ensemble stepping and the tile autotuner
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchConfig {
+    double wait_limit_s = 2.0;
+    int test_stall = 0;
+};
+BatchConfig g_batch_cfg;
+
+// Tile depth (z planes per work item) chosen by the autotuner, per grid shape.
+std::mutex g_tune_mu;
+std::map<std::string, int> *g_tune = nullptr;
+bool g_tune_loaded = false;
+
+std::string shape_key(const osb_grid_desc &d) {
+    char b[128];
+    snprintf(b, sizeof b, "%dx%dx%d/o%d/%s/v%d", d.nx, d.ny, d.nz, d.order, d.precision == OSB_FP64 ? "fp64" : "fp32",
+             d.visc_form);
+    return b;
+}
+
+// Cache file: one "key tz" pair per line at $OSB_AUTOTUNE_CACHE.
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    if (!g_tune) g_tune = new std::map<std::string, int>();
+    const char *path = getenv("OSB_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char key[128];
+    int tz;
+    while (fscanf(f, "%127s %d", key, &tz) == 2)
+        if (tz >= 1 && tz <= 64) (*g_tune)[key] = tz;
+    fclose(f);
+}
+
+void tune_save_locked() {
+    const char *path = getenv("OSB_AUTOTUNE_CACHE");
+    if (!path || !g_tune) return;
+    FILE *f = fopen(path, "w");
+    if (!f) return;
+    for (auto &kv : *g_tune) fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+    fclose(f);
+}
+
+int tile_depth(const osb_grid_desc &d) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune->find(shape_key(d));
+    return it == g_tune->end() ? 4 : it->second;
+}
+
+osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
+    if (!grids || n < 1 || n > MAXB || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "batch: need 1..128 grids, nsteps >= 0");
     for (int i = 0; i < n; ++i)
         if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
-    for (int i = 1; i < n; ++i)
-        if (grids[i]->st != grids[0]->st) return fail(OSB_ERR_INVALID_ARG, "batch grids must share one stream");
-    for (int s = 0; s < nsteps; ++s)
-        for (int i = 0; i < n; ++i) {
-            osb_status st = rk3_one_step(grids[i]);
-            if (st != OSB_OK) return st;
+    const osb_grid *g0 = grids[0];
+    for (int i = 1; i < n; ++i) {
+        const osb_grid *g = grids[i];
+        if (g->st != g0->st) return fail(OSB_ERR_INVALID_ARG, "batch grids must share one stream");
+        if (g->desc.order != g0->desc.order || g->desc.precision != g0->desc.precision ||
+            g->desc.visc_form != g0->desc.visc_form)
+            return fail(OSB_ERR_UNSUPPORTED, "batch grids must share order, precision and viscous form");
+        for (int j = 0; j < i; ++j)
+            if (grids[j] == g) return fail(OSB_ERR_INVALID_ARG, "a grid appears twice in the batch");
+    }
+    if (nsteps == 0) return OSB_OK;
+    cudaStream_t st = g0->st;
+    BatchParams P;
+    memset(&P, 0, sizeof(P));
+    P.n = n;
+    P.prefix[0] = 0;
+    std::string key = std::to_string(nsteps) + "|" + std::to_string(g_batch_cfg.test_stall) + "|" +
+                      std::to_string((long long)(g_batch_cfg.wait_limit_s * 1e9));
+    for (int i = 0; i < n; ++i) {
+        osb_grid *g = grids[i];
+        osb_status s0 = ensure_f32_copy(g);
+        if (s0 != OSB_OK) return s0;
+        BatchInst rec;
+        memset(&rec, 0, sizeof(rec));
+        for (int par = 0; par < 2; ++par)
+            for (int k = 0; k < 3; ++k) rec.st[par][k] = stage_args(g, par, k);
+        rec.tz = tile_depth(g->desc);
+        rec.tiles_x = (g->d.nx + BX - 1) / BX;
+        rec.tiles_y = (g->d.ny + BY - 1) / BY;
+        rec.tiles_z = (g->d.nz + rec.tz - 1) / rec.tz;
+        cudaError_t e = cudaMemcpyAsync(g->batch_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "batch record upload");
+        const long long tiles = (long long)rec.tiles_x * rec.tiles_y * rec.tiles_z;
+        if (P.prefix[i] + tiles > 0x3fffffff) return fail(OSB_ERR_INVALID_ARG, "batch too large");
+        P.prefix[i + 1] = P.prefix[i] + (int)tiles;
+        P.rec[i] = g->batch_rec;
+        P.p0[i] = g->cur;
+        char b[64];
+        snprintf(b, sizeof b, "|%p:%d:%d", (void *)g, g->cur, rec.tz);
+        key += b;
+    }
+    P.tiles_total = P.prefix[n];
+    P.total_items = (long long)nsteps * 9 * P.tiles_total;
+    if ((long long)nsteps * 9 * (P.prefix[n] - P.prefix[n - 1]) > 0xffffffffLL)
+        return fail(OSB_ERR_INVALID_ARG, "batch: too many steps for the 32-bit completion counters");
+    P.timeout_ns = (long long)(g_batch_cfg.wait_limit_s * 1e9);
+    P.inject_stall = g_batch_cfg.test_stall;
+    char *ctl = g0->batch_ctl;
+    P.counter = (unsigned long long *)ctl;
+    P.err = (int *)(ctl + 8);
+    P.done = (unsigned *)(ctl + 16);
+
+    // one memset and one persistent launch, captured once per (grids, parity,
+    // nsteps) and replayed as a CUDA graph
+    osb_grid *lead = grids[0];
+    if (!lead->graphs) lead->graphs = new std::map<std::string, cudaGraphExec_t>();
+    cudaGraphExec_t exec = nullptr;
+    auto it = lead->graphs->find(key);
+    if (it != lead->graphs->end()) {
+        exec = it->second;
+    } else {
+        // capture on a library-owned stream (the caller's may be the legacy
+        // default stream, which cannot be captured); the graph is then
+        // launched on the caller's stream
+        if (!lead->capture_st) {
+            cudaError_t ec = cudaStreamCreateWithFlags(&lead->capture_st, cudaStreamNonBlocking);
+            if (ec != cudaSuccess) {
+                lead->capture_st = nullptr;
+                return cuda_fail(ec, "batch capture stream");
+            }
         }
+        cudaStream_t cs = lead->capture_st;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
+        cudaError_t e1 = cudaMemsetAsync(ctl, 0, 16 + sizeof(unsigned) * MAXB, cs);
+        cudaError_t e2 = launch_batch(P, g0->desc.order, g0->desc.precision, g0->desc.visc_form, cs);
+        e = cudaStreamEndCapture(cs, &graph);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e), "batch capture");
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
+        if (lead->graphs->size() >= 8) {
+            for (auto &kv : *lead->graphs) cudaGraphExecDestroy(kv.second);
+            lead->graphs->clear();
+        }
+        (*lead->graphs)[key] = exec;
+    }
+    cudaError_t e = cudaGraphLaunch(exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+    int herr = 0;
+    e = cudaMemcpyAsync(&herr, P.err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch status copy");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    for (int i = 0; i < n; ++i) {
+        osb_grid *g = grids[i];
+        if (nsteps & 1) g->cur = 1 - g->cur;
+        g->qc = g->cur;
+        g->step += nsteps;
+        g->t = g->step * g->prm.dt;
+    }
+    if (herr) return fail(OSB_ERR_TIMEOUT, "batch: a per-instance wait exceeded its time limit; grid states are undefined");
+    return OSB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) { return batch_run(grids, n, nsteps); }
+
+osb_status osb_batch_configure(double wait_limit_seconds, int test_stall) {
+    if (!(wait_limit_seconds > 0) || wait_limit_seconds > 3600)
+        return fail(OSB_ERR_INVALID_ARG, "wait limit must be in (0, 3600] seconds");
+    g_batch_cfg.wait_limit_s = wait_limit_seconds;
+    g_batch_cfg.test_stall = test_stall ? 1 : 0;
+    return OSB_OK;
+}
+
+osb_status osb_autotune(osb_grid *g, int trial_steps, int *best_tz) {
+    if (!g || trial_steps < 1) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    const size_t n = g->d.n;
+    std::vector<double> saved;
+    try {
+        saved.resize(5 * n);
+    } catch (...) {
+        return fail(OSB_ERR_INVALID_ARG, "host allocation failed");
+    }
+    const int cur0 = g->cur;
+    const double t0 = g->t;
+    const long long step0 = g->step;
+    osb_status s = osb_get_state(g, saved.data());
+    if (s != OSB_OK) return s;
+    const std::string key = shape_key(g->desc);
+    const int cand[] = {1, 2, 4, 8, 16};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(OSB_ERR_CUDA, "autotune: event create failed");
+    int best = 4;
+    float best_ms = 1e30f;
+    for (int tz : cand) {
+        if (tz > g->d.nz && tz != 1) continue;
+        {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            tune_load_locked();
+            (*g_tune)[key] = tz;
+        }
+        osb_grid *one[1] = {g};
+        s = batch_run(one, 1, 1);  // warm-up (captures the graph)
+        if (s != OSB_OK) break;
+        cudaEventRecord(e0, g->st);
+        s = batch_run(one, 1, trial_steps);
+        cudaEventRecord(e1, g->st);
+        if (s != OSB_OK) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = tz;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        (*g_tune)[key] = best;
+        tune_save_locked();
+    }
+    // restore the state the call started from
+    g->cur = cur0;
+    g->qc = cur0;
+    osb_status r = osb_set_state(g, saved.data());
+    g->t = t0;
+    g->step = step0;
+    if (s != OSB_OK) return s;
+    if (r != OSB_OK) return r;
+    if (best_tz) *best_tz = best;
     return OSB_OK;
 }
 

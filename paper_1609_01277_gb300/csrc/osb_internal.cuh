@@ -17,6 +17,7 @@
 namespace osb {
 
 constexpr int MAXR = 6;  // orders 2..12
+constexpr int BX = 32, BY = 8;  // thread block / tile of the per-point stage kernels
 
 // Point-wise intermediate fields written by the primitive and gradient
 // kernels of a stage and read by the residual kernel.
@@ -101,6 +102,31 @@ OrderKernels kernels_o6();
 OrderKernels kernels_o8();
 OrderKernels kernels_o10();
 OrderKernels kernels_o12();
+
+// Persistent ensemble kernel (batch.cu).
+constexpr int MAXB = 128;  // instances per batch
+
+struct BatchInst {
+    StageArgs st[2][3];  // [parity of (cur)][RK stage]
+    int tz;              // z planes per tile
+    int tiles_x, tiles_y, tiles_z;
+};
+
+struct BatchParams {
+    int n;
+    int tiles_total;       // items per phase sequence, all instances
+    long long total_items;
+    long long timeout_ns;  // bound on every dependency wait
+    int inject_stall;      // test control: make the first wait unreachable
+    const BatchInst *rec[MAXB];
+    int prefix[MAXB + 1];  // tile prefix sums
+    int p0[MAXB];          // parity of each instance at the first step
+    unsigned long long *counter;
+    unsigned *done;
+    int *err;
+};
+
+cudaError_t launch_batch(const BatchParams &P, int order, int precision, int visc_form, cudaStream_t st);
 
 // Host helpers shared by the translation units (defined in osb_api.cu).
 Phys make_phys(const osb_params &prm);

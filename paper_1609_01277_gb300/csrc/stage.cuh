@@ -72,32 +72,39 @@ struct Nbr {
     __device__ __forceinline__ int center() const { return z[R] + y[R] + x[R]; }
 };
 
-template <typename T, typename P>
+// Global-load policy.  LD_NC: read-only path (data written before the launch).
+// LD_CG: L2 only, for data that other CTAs of the same (persistent) launch
+// wrote -- the per-SM L1 is not coherent with those writes.
+enum LoadPolicy { LD_NC = 0, LD_CG = 1 };
+
+template <int POL, typename T, typename P>
 __device__ __forceinline__ T ld(const P *p) {
-    return T(__ldg(p));
+    if constexpr (POL == LD_CG)
+        return T(__ldcg(p));
+    else
+        return T(__ldg(p));
 }
 
 // First derivative along AX of field f at the point (weights already / h).
-template <int R, int AX, typename T, typename P>
+template <int R, int AX, int POL = LD_NC, typename T, typename P>
 __device__ __forceinline__ T D1(const P *__restrict__ f, const Nbr<R> &nb, const Coef<T> &c) {
     T s = T(0);
 #pragma unroll
     for (int k = R; k >= 1; --k)
-        s = fma(c.d1[AX][k], ld<T>(f + nb.template at<AX>(k)) - ld<T>(f + nb.template at<AX>(-k)), s);
+        s = fma(c.d1[AX][k], ld<POL, T>(f + nb.template at<AX>(k)) - ld<POL, T>(f + nb.template at<AX>(-k)), s);
     return s;
 }
 
 // Second derivative along AX (weights already / h^2).
-template <int R, int AX, typename T, typename P>
+template <int R, int AX, int POL = LD_NC, typename T, typename P>
 __device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R> &nb, const Coef<T> &c) {
-    T s = c.d2[AX][0] * ld<T>(f + nb.center());
+    T s = c.d2[AX][0] * ld<POL, T>(f + nb.center());
 #pragma unroll
     for (int k = R; k >= 1; --k)
-        s = fma(c.d2[AX][k], ld<T>(f + nb.template at<AX>(k)) + ld<T>(f + nb.template at<AX>(-k)), s);
+        s = fma(c.d2[AX][k], ld<POL, T>(f + nb.template at<AX>(k)) + ld<POL, T>(f + nb.template at<AX>(-k)), s);
     return s;
 }
 
-constexpr int BX = 32, BY = 8;
 
 // Exact float -> double and round-to-nearest-even double -> float, on the
 // integer pipes (GB300 issues FP64 instructions, conversions included, at
@@ -135,18 +142,16 @@ __device__ __forceinline__ float d2f_bits(double d) {
 // ---------------------------------------------------------------------------
 // k_prim: primitives and the point-wise momentum fluxes
 // ---------------------------------------------------------------------------
-template <typename S, typename T>
-__global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
-    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
-    if (x >= a.d.nx || y >= a.d.ny) return;
+template <int POL, typename S, typename T>
+__device__ __forceinline__ void prim_point(const StageArgs &a, int x, int y, int z) {
     const int i = (z * a.d.ny + y) * a.d.nx + x;
     const S *Q = static_cast<const S *>(a.src);
     const size_t qs = a.src_stride;
     T *aux = static_cast<T *>(a.aux);
     const size_t as = a.aux_stride;
 
-    const T rho = T(Q[i]), mx = T(Q[qs + i]), my = T(Q[2 * qs + i]), mz = T(Q[3 * qs + i]);
-    const T e = T(Q[4 * qs + i]);
+    const T rho = ld<POL, T>(Q + i), mx = ld<POL, T>(Q + qs + i), my = ld<POL, T>(Q + 2 * qs + i);
+    const T mz = ld<POL, T>(Q + 3 * qs + i), e = ld<POL, T>(Q + 4 * qs + i);
     const T rinv = T(1) / rho;
     const T u = mx * rinv, v = my * rinv, w = mz * rinv;
     const T ke = T(0.5) * (mx * u + my * v + mz * w);
@@ -166,13 +171,18 @@ __global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
     aux[A_PYZ * as + i] = hmy * w;
 }
 
+template <typename S, typename T>
+__global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+    if (x >= a.d.nx || y >= a.d.ny) return;
+    prim_point<LD_NC, S, T>(a, x, y, z);
+}
+
 // ---------------------------------------------------------------------------
 // k_grad: velocity gradient -> div u, tau_ij, energy flux, viscous g-term
 // ---------------------------------------------------------------------------
-template <typename S, typename T, int R, bool VB>
-__global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
-    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
-    if (x >= a.d.nx || y >= a.d.ny) return;
+template <int POL, typename S, typename T, int R, bool VB>
+__device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int z) {
     Nbr<R> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
@@ -181,27 +191,27 @@ __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
     const size_t as = a.aux_stride;
     const T *U = aux + A_U * as, *V = aux + A_V * as, *W = aux + A_W * as;
 
-    const T gxx = D1<R, 0>(U, nb, c), gxy = D1<R, 1>(U, nb, c), gxz = D1<R, 2>(U, nb, c);
-    const T gyx = D1<R, 0>(V, nb, c), gyy = D1<R, 1>(V, nb, c), gyz = D1<R, 2>(V, nb, c);
-    const T gzx = D1<R, 0>(W, nb, c), gzy = D1<R, 1>(W, nb, c), gzz = D1<R, 2>(W, nb, c);
+    const T gxx = D1<R, 0, POL>(U, nb, c), gxy = D1<R, 1, POL>(U, nb, c), gxz = D1<R, 2, POL>(U, nb, c);
+    const T gyx = D1<R, 0, POL>(V, nb, c), gyy = D1<R, 1, POL>(V, nb, c), gyz = D1<R, 2, POL>(V, nb, c);
+    const T gzx = D1<R, 0, POL>(W, nb, c), gzy = D1<R, 1, POL>(W, nb, c), gzz = D1<R, 2, POL>(W, nb, c);
     const T div = gxx + gyy + gzz;
     const T ir = T(a.ph.inv_re);
     const T tdiv = T(2.0 / 3.0) * div;
     const T txx = ir * (gxx + gxx - tdiv), tyy = ir * (gyy + gyy - tdiv), tzz = ir * (gzz + gzz - tdiv);
     const T txy = ir * (gxy + gyx), txz = ir * (gxz + gzx), tyz = ir * (gyz + gzy);
-    const T u = aux[A_U * as + i], v = aux[A_V * as + i], w = aux[A_W * as + i];
-    const T p = aux[A_P * as + i];
+    const T u = ld<POL, T>(aux + A_U * as + i), v = ld<POL, T>(aux + A_V * as + i);
+    const T w = ld<POL, T>(aux + A_W * as + i), p = ld<POL, T>(aux + A_P * as + i);
     const S *Q = static_cast<const S *>(a.src);
-    const T hE = fma(T(0.5), T(Q[4 * a.src_stride + i]), p);
+    const T hE = fma(T(0.5), ld<POL, T>(Q + 4 * a.src_stride + i), p);
     aux[A_DIV * as + i] = div;
     if (!VB) {
         aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
         aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
         aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
         const T ir3 = ir * T(1.0 / 3.0);
-        aux[A_PXX * as + i] -= ir3 * (gyy + gzz);
-        aux[A_PYY * as + i] -= ir3 * (gxx + gzz);
-        aux[A_PZZ * as + i] -= ir3 * (gxx + gyy);
+        aux[A_PXX * as + i] = ld<POL, T>(aux + A_PXX * as + i) - ir3 * (gyy + gzz);
+        aux[A_PYY * as + i] = ld<POL, T>(aux + A_PYY * as + i) - ir3 * (gxx + gzz);
+        aux[A_PZZ * as + i] = ld<POL, T>(aux + A_PZZ * as + i) - ir3 * (gxx + gyy);
     } else {
         aux[A_FX * as + i] = hE * u;
         aux[A_FY * as + i] = hE * v;
@@ -214,13 +224,18 @@ __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
     }
 }
 
+template <typename S, typename T, int R, bool VB>
+__global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+    if (x >= a.d.nx || y >= a.d.ny) return;
+    grad_point<LD_NC, S, T, R, VB>(a, x, y, z);
+}
+
 // ---------------------------------------------------------------------------
 // k_resid: residual and RK update (MODE 0) or residual only (MODE 1)
 // ---------------------------------------------------------------------------
-template <typename S, typename T, int R, int MODE, bool VB>
-__global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
-    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
-    if (x >= a.d.nx || y >= a.d.ny) return;
+template <int POL, typename S, typename T, int R, int MODE, bool VB>
+__device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, int z) {
     Nbr<R> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
@@ -230,16 +245,16 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     const T *aux = static_cast<const T *>(a.aux);
     const size_t as = a.aux_stride;
 
-    const T u = aux[A_U * as + i], v = aux[A_V * as + i], w = aux[A_W * as + i];
-    const T div = aux[A_DIV * as + i];
+    const T u = ld<POL, T>(aux + A_U * as + i), v = ld<POL, T>(aux + A_V * as + i);
+    const T w = ld<POL, T>(aux + A_W * as + i), div = ld<POL, T>(aux + A_DIV * as + i);
 
     T res[5];
     // advective + dilatation half of the skew-symmetric form, per field
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
         const S *f = Q + m * qs;
-        const T dx = D1<R, 0>(f, nb, c), dy = D1<R, 1>(f, nb, c), dz = D1<R, 2>(f, nb, c);
-        res[m] = T(-0.5) * fma(u, dx, fma(v, dy, fma(w, dz, T(f[i]) * div)));
+        const T dx = D1<R, 0, POL>(f, nb, c), dy = D1<R, 1, POL>(f, nb, c), dz = D1<R, 2, POL>(f, nb, c);
+        res[m] = T(-0.5) * fma(u, dx, fma(v, dy, fma(w, dz, ld<POL, T>(f + i) * div)));
         // mass flux d_j(m_j/2): m_j is field 1+j, differentiated along j
         if (m == 1) res[0] = fma(T(-0.5), dx, res[0]);
         if (m == 2) res[0] = fma(T(-0.5), dy, res[0]);
@@ -248,32 +263,32 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     // momentum fluxes
     const T *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
     const T *Pxy = aux + A_PXY * as, *Pxz = aux + A_PXZ * as, *Pyz = aux + A_PYZ * as;
-    res[1] -= D1<R, 0>(Pxx, nb, c) + D1<R, 1>(Pxy, nb, c) + D1<R, 2>(Pxz, nb, c);
-    res[2] -= D1<R, 0>(Pxy, nb, c) + D1<R, 1>(Pyy, nb, c) + D1<R, 2>(Pyz, nb, c);
-    res[3] -= D1<R, 0>(Pxz, nb, c) + D1<R, 1>(Pyz, nb, c) + D1<R, 2>(Pzz, nb, c);
+    res[1] -= D1<R, 0, POL>(Pxx, nb, c) + D1<R, 1, POL>(Pxy, nb, c) + D1<R, 2, POL>(Pxz, nb, c);
+    res[2] -= D1<R, 0, POL>(Pxy, nb, c) + D1<R, 1, POL>(Pyy, nb, c) + D1<R, 2, POL>(Pyz, nb, c);
+    res[3] -= D1<R, 0, POL>(Pxz, nb, c) + D1<R, 1, POL>(Pyz, nb, c) + D1<R, 2, POL>(Pzz, nb, c);
     // energy flux
-    res[4] -= D1<R, 0>(aux + A_FX * as, nb, c) + D1<R, 1>(aux + A_FY * as, nb, c) +
-              D1<R, 2>(aux + A_FZ * as, nb, c);
+    res[4] -= D1<R, 0, POL>(aux + A_FX * as, nb, c) + D1<R, 1, POL>(aux + A_FY * as, nb, c) +
+              D1<R, 2, POL>(aux + A_FZ * as, nb, c);
     // viscous Laplacians: (1/Re)[sum_j L_j u_i + L_i u_i / 3]
     const T ir = T(a.ph.inv_re), f43 = T(4.0 / 3.0);
     {
         const T *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as;
-        T vx = ir * fma(f43, D2<R, 0>(Uf, nb, c), D2<R, 1>(Uf, nb, c) + D2<R, 2>(Uf, nb, c));
-        T vy = ir * fma(f43, D2<R, 1>(Vf, nb, c), D2<R, 0>(Vf, nb, c) + D2<R, 2>(Vf, nb, c));
-        T vz = ir * fma(f43, D2<R, 2>(Wf, nb, c), D2<R, 0>(Wf, nb, c) + D2<R, 1>(Wf, nb, c));
+        T vx = ir * fma(f43, D2<R, 0, POL>(Uf, nb, c), D2<R, 1, POL>(Uf, nb, c) + D2<R, 2, POL>(Uf, nb, c));
+        T vy = ir * fma(f43, D2<R, 1, POL>(Vf, nb, c), D2<R, 0, POL>(Vf, nb, c) + D2<R, 2, POL>(Vf, nb, c));
+        T vz = ir * fma(f43, D2<R, 2, POL>(Wf, nb, c), D2<R, 0, POL>(Wf, nb, c) + D2<R, 1, POL>(Wf, nb, c));
         if (VB) {
             // the D_i g_i / 3 part of the viscous momentum term, kept separate
             const T ir3 = ir * T(1.0 / 3.0);
-            vx = fma(ir3, D1<R, 0>(aux + A_GX * as, nb, c), vx);
-            vy = fma(ir3, D1<R, 1>(aux + A_GY * as, nb, c), vy);
-            vz = fma(ir3, D1<R, 2>(aux + A_GZ * as, nb, c), vz);
-            res[4] += fma(u, vx, fma(v, vy, fma(w, vz, aux[A_TG * as + i])));
+            vx = fma(ir3, D1<R, 0, POL>(aux + A_GX * as, nb, c), vx);
+            vy = fma(ir3, D1<R, 1, POL>(aux + A_GY * as, nb, c), vy);
+            vz = fma(ir3, D1<R, 2, POL>(aux + A_GZ * as, nb, c), vz);
+            res[4] += fma(u, vx, fma(v, vy, fma(w, vz, ld<POL, T>(aux + A_TG * as + i))));
         }
         res[1] += vx;
         res[2] += vy;
         res[3] += vz;
         const T *Tf = aux + A_T * as;
-        res[4] = fma(T(a.ph.kappa), D2<R, 0>(Tf, nb, c) + D2<R, 1>(Tf, nb, c) + D2<R, 2>(Tf, nb, c), res[4]);
+        res[4] = fma(T(a.ph.kappa), D2<R, 0, POL>(Tf, nb, c) + D2<R, 1, POL>(Tf, nb, c) + D2<R, 2, POL>(Tf, nb, c), res[4]);
     }
 
     if (MODE == 0) {
@@ -281,7 +296,7 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
         if constexpr (sizeof(T) == 8) {
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
-                const double Ui = a.U_in[m * a.u_stride + i];
+                const double Ui = ld<POL, double>(a.U_in + m * a.u_stride + i);
                 const double Rm = double(res[m]);
                 a.U_out[m * a.u_stride + i] = fma(a.beta_dt, Rm, Ui);
                 if (qo) qo[m * a.q_stride + i] = T(fma(a.alpha_dt, Rm, Ui));
@@ -294,7 +309,7 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
             const float bdt = float(a.beta_dt), adt = float(a.alpha_dt);
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
-                const double Ui = a.U_in[m * a.u_stride + i];
+                const double Ui = ld<POL, double>(a.U_in + m * a.u_stride + i);
                 const double Un = Ui + f2d_bits(bdt * float(res[m]));
                 a.U_out[m * a.u_stride + i] = Un;
                 if (qo) qo[m * a.q_stride + i] = T(fmaf(adt, float(res[m]), d2f_bits(Ui)));
@@ -305,6 +320,13 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
 #pragma unroll
         for (int m = 0; m < 5; ++m) a.R_out[m * a.R_stride + i] = double(res[m]);
     }
+}
+
+template <typename S, typename T, int R, int MODE, bool VB>
+__global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+    if (x >= a.d.nx || y >= a.d.ny) return;
+    resid_point<LD_NC, S, T, R, MODE, VB>(a, x, y, z);
 }
 
 template <typename S, typename T, int R, bool VB>

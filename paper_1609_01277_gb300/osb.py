@@ -27,7 +27,7 @@ STATUS = {0: "OSB_OK", 1: "OSB_ERR_INVALID_ARG", 2: "OSB_ERR_UNSUPPORTED", 3: "O
 EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_grid_destroy",
            "osb_init_taylor_green", "osb_set_state", "osb_get_state", "osb_set_state_device",
            "osb_get_state_device", "osb_residual", "osb_rk3_step", "osb_diagnostics",
-           "osb_batch_step", "osb_diagnostics_noalloc", "osb_profile_start", "osb_profile_stop",
+           "osb_batch_step", "osb_batch_configure", "osb_autotune", "osb_diagnostics_noalloc", "osb_profile_start", "osb_profile_stop",
            "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
@@ -83,6 +83,8 @@ def load(path: str | None = None):
     L.osb_rk3_step.argtypes = [vp, ctypes.c_int]
     L.osb_diagnostics.argtypes = [vp, ctypes.POINTER(Diag)]
     L.osb_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
+    L.osb_batch_configure.argtypes = [ctypes.c_double, ctypes.c_int]
+    L.osb_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.osb_diagnostics_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, vp, vp]
     L.osb_profile_start.argtypes = [vp, ctypes.c_int]
     L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
@@ -244,5 +246,17 @@ def diagnostics_noalloc(Q_dev, cfg: Config, out_dev, stream=None) -> None:
 
 
 def batch_step(grids, nsteps: int) -> None:
+    """One persistent, graph-captured launch advancing every grid nsteps steps."""
     arr = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
     check(load().osb_batch_step(arr, len(grids), int(nsteps)), "osb_batch_step")
+
+
+def batch_configure(wait_limit_seconds: float = 2.0, test_stall: bool = False) -> None:
+    check(load().osb_batch_configure(float(wait_limit_seconds), int(bool(test_stall))), "osb_batch_configure")
+
+
+def autotune(grid: "Grid", trial_steps: int = 3) -> int:
+    """Pick the ensemble tile depth for this grid's shape (state is restored)."""
+    tz = ctypes.c_int(0)
+    check(load().osb_autotune(grid.handle, int(trial_steps), ctypes.byref(tz)), "osb_autotune")
+    return tz.value

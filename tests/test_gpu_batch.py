@@ -1,0 +1,132 @@
+"""Ensemble stepping: one persistent, graph-captured launch over grids of
+uneven sizes and parameters (osb_batch_step), its bounded waits, and the
+tile autotuner."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import oracle as orc
+from paper_1609_01277_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osb():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_01277_gb300 import build
+    build.build()
+    from paper_1609_01277_gb300 import osb as m
+    m.load()
+    m.batch_configure(2.0, False)
+    return m
+
+
+def _ensemble(osb, specs, precision, order=4, seed=3):
+    grids = []
+    for i, (n, Re, M, dt) in enumerate(specs):
+        g = osb.Grid(osb.Config(n, n, n, order=order, precision=precision, Re=Re, Mach=M, dt=dt))
+        g.init_taylor_green(inputs.gaussian_noise(n, n, n, seed + i), 1e-3)
+        grids.append(g)
+    return grids
+
+
+SPECS = [(16, 1600.0, 0.1, 2e-3), (24, 400.0, 0.2, 1.5e-3), (12, 3000.0, 0.05, 3e-3), (20, 100.0, 0.3, 1e-3)]
+
+
+def test_batch_equals_per_grid_steps_bitwise_fp64(osb):
+    a = _ensemble(osb, SPECS, osb.OSB_FP64)
+    b = _ensemble(osb, SPECS, osb.OSB_FP64)
+    for g in a:
+        g.step(7)
+    osb.batch_step(b, 3)      # odd count: the register roles flip
+    osb.batch_step(b, 4)      # different parity pattern, new graph
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.get_state(), gb.get_state())
+        assert gb.diagnostics()["step"] == 7
+
+
+def test_batch_graph_replay_and_mixed_parity(osb):
+    a = _ensemble(osb, SPECS, osb.OSB_FP64)
+    b = _ensemble(osb, SPECS, osb.OSB_FP64)
+    b[1].step(1)              # instances start with different register parities
+    a[1].step(1)
+    for _ in range(3):
+        osb.batch_step(b, 2)  # same key: the captured graph is replayed
+    for g in a:
+        g.step(6)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.get_state(), gb.get_state())
+
+
+@pytest.mark.parametrize("order", [4, 8])
+def test_batch_fp32_close_to_oracle(osb, order):
+    specs = [(16, 800.0, 0.15, 2e-3), (24, 1600.0, 0.1, 1e-3)]
+    grids = _ensemble(osb, specs, osb.OSB_FP32, order=order, seed=11)
+    osb.batch_step(grids, 6)
+    for i, ((n, Re, M, dt), g) in enumerate(zip(specs, grids)):
+        case = orc.Case(n, n, n, order=order, Re=Re, Mach=M, dt=dt)
+        Qo = orc.rk3_step(case, orc.tgv_init(case, inputs.gaussian_noise(n, n, n, 11 + i), 1e-3), 6)
+        Q = g.get_state()
+        mnorm = np.linalg.norm(Qo[1:4].ravel())
+        for m in range(5):
+            scale = mnorm if 1 <= m <= 3 else np.linalg.norm(Qo[m].ravel())
+            assert np.linalg.norm((Q[m] - Qo[m]).ravel()) / scale < 1e-5
+
+
+def test_batch_fp64_matches_oracle(osb):
+    specs = [(12, 500.0, 0.2, 2e-3), (16, 1600.0, 0.1, 2e-3)]
+    grids = _ensemble(osb, specs, osb.OSB_FP64, order=6, seed=21)
+    osb.batch_step(grids, 3)
+    for i, ((n, Re, M, dt), g) in enumerate(zip(specs, grids)):
+        case = orc.Case(n, n, n, order=6, Re=Re, Mach=M, dt=dt)
+        Qo = orc.rk3_step(case, orc.tgv_init(case, inputs.gaussian_noise(n, n, n, 21 + i), 1e-3), 3)
+        Q = g.get_state()
+        for m in range(5):
+            assert np.linalg.norm(Q[m] - Qo[m]) / np.linalg.norm(Qo[m]) < 1e-12
+
+
+def test_batch_wait_limit_reports_timeout_and_context_survives(osb):
+    """A wait on a count that nothing reaches runs out after its limit: the call
+    returns OSB_ERR_TIMEOUT (no trap, no hang) and the GPU keeps working."""
+    grids = _ensemble(osb, SPECS[:2], osb.OSB_FP64)
+    osb.batch_configure(0.05, True)
+    try:
+        with pytest.raises(osb.OsbError) as ei:
+            osb.batch_step(grids, 2)
+        assert ei.value.status == 5
+    finally:
+        osb.batch_configure(2.0, False)
+    fresh = _ensemble(osb, SPECS[:2], osb.OSB_FP64)
+    ref = _ensemble(osb, SPECS[:2], osb.OSB_FP64)
+    osb.batch_step(fresh, 2)
+    for g in ref:
+        g.step(2)
+    for a, b in zip(fresh, ref):
+        assert np.array_equal(a.get_state(), b.get_state())
+
+
+def test_batch_rejects_mixed_configurations(osb):
+    a = osb.Grid(osb.Config(8, 8, 8, order=4))
+    b = osb.Grid(osb.Config(8, 8, 8, order=8))
+    with pytest.raises(osb.OsbError) as ei:
+        osb.batch_step([a, b], 1)
+    assert ei.value.status == 2
+    with pytest.raises(osb.OsbError):
+        osb.batch_step([a, a], 1)
+
+
+def test_autotune_restores_state(osb, tmp_path, monkeypatch):
+    g = _ensemble(osb, [(24, 1600.0, 0.1, 1e-3)], osb.OSB_FP64)[0]
+    g.step(2)
+    before = g.get_state()
+    d0 = g.diagnostics()
+    tz = osb.autotune(g, trial_steps=2)
+    assert tz in (1, 2, 4, 8, 16)
+    assert np.array_equal(g.get_state(), before)
+    d1 = g.diagnostics()
+    assert d1["step"] == d0["step"] and d1["t"] == d0["t"]
+    g.step(1)  # still usable
