@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--ensemble-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -241,6 +243,55 @@ def ke_series(torch, g, steps):
     return out
 
 
+def ensemble_specs(count=64, seed=7):
+    """The uneven Taylor-Green ensemble: N from {32,48,64,96,128}, Re in
+    [100, 3200], M in [0.05, 0.3]; dt = 3.385e-3 (64/N) 11/(1 + 1/M) keeps the
+    paper's acoustic Courant number of the 64^3, M = 0.1 case."""
+    from paper_1609_01277_gb300 import inputs
+    out = []
+    for e in inputs.ensemble(count, seed):
+        e["dt"] = BASE_DT_64 * (64.0 / e["n"]) * 11.0 / (1.0 + 1.0 / e["Mach"])
+        out.append(e)
+    return out
+
+
+def run_ensemble(torch, osb, inputs, steps, precision):
+    specs = ensemble_specs()
+    prec = osb.OSB_FP64 if precision == "fp64" else osb.OSB_FP32
+    grids = []
+    for i, e in enumerate(specs):
+        n = e["n"]
+        g = osb.Grid(osb.Config(n, n, n, order=4, precision=prec, Re=e["Re"], Mach=e["Mach"], dt=e["dt"]))
+        g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
+        grids.append(g)
+    tuned = {}
+    for g in grids:
+        if g.cfg.nx not in tuned:
+            tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
+    pts = sum(g.cfg.n for g in grids)
+    osb.batch_step(grids, steps)          # warm-up + graph capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    osb.batch_step(grids, steps)          # synchronises internally
+    t_batch = time.perf_counter() - t0
+    for g in grids:                       # the same work as per-grid launches
+        g.step(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for g in grids:
+            g.step(1)
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    ke = [g.diagnostics()["ke"] for g in grids[:4]]
+    del grids
+    torch.cuda.empty_cache()
+    return {"instances": len(specs), "points": pts, "steps": steps, "tile_depth": tuned,
+            "value": steps * 3 * pts / t_batch, "ms_per_step": 1e3 * t_batch / steps,
+            "per_grid_launch_value": steps * 3 * pts / t_seq, "speedup_vs_per_grid_launches": t_seq / t_batch,
+            "ke_first4": ke, "launches_per_step": 1, "per_grid_launches_per_step": 9 * len(specs)}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -358,6 +409,13 @@ def run_ours(args):
             variants[f"order{order}_fp32"]["ke_err_vs_fp64"] = err
             variants[f"order{order}_fp32"]["speedup_vs_fp64"] = (
                 variants[f"order{order}_fp32"]["value"] / variants[f"order{order}_fp64"]["value"])
+
+    if not args.no_ensemble and world == 1:
+        for prec in ("fp64", "fp32"):
+            variants[f"ensemble64_order4_{prec}"] = run_ensemble(torch, osb, inputs, args.ensemble_steps, prec)
+        e64, e32 = variants["ensemble64_order4_fp64"], variants["ensemble64_order4_fp32"]
+        e32["speedup_vs_fp64_ensemble"] = e32["value"] / e64["value"]
+        e32["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(e32["ke_first4"], e64["ke_first4"]))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
