@@ -82,6 +82,7 @@ typedef struct {
 } osb_diag;
 
 typedef struct osb_grid osb_grid; /* opaque; owns host metadata only */
+typedef struct osb_closure osb_closure; /* opaque; learned residual correction */
 
 /* Bytes of device memory the caller must provide for the state registers of
  * the low-storage RK3 scheme (two FP64 accumulators, two stage registers in
@@ -206,6 +207,56 @@ osb_status osb_autotune(osb_grid *grid, int trial_steps, int *best_tz);
  * routine is called. */
 osb_status osb_diagnostics_noalloc(const double *Q_dev, int nx, int ny, int nz, int order,
                                    const osb_params *params, double *out_dev, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Learned residual correction ("closure") for coarse grids.  Not in the paper
+ * (its future work lists LES models, Section 1); a spec extension.
+ * Network: three 3x3x3 periodic convolutions 5 -> 32 -> 32 -> 5 with ReLU
+ * after the first two; input: the 5 conserved fields normalised per channel
+ * ((Q_c - mean_c)/std_c); output y scaled per channel by out_std_c and added
+ * to the residual R in every RK stage.  BF16 weights and activations, FP32
+ * accumulation on the tensor cores.  Grid sizes must be multiples of (8,4,4).
+ * ------------------------------------------------------------------------ */
+
+/* FP32 master parameters: W1[32][5][27] b1[32] W2[32][32][27] b2[32]
+ * W3[5][32][27] b3[5] (tap k = (dz+1)*9 + (dy+1)*3 + (dx+1), cross-correlation
+ * y(p) = b + sum_k W[k] x(p + offset_k)).  36,357 values. */
+size_t osb_closure_param_count(void);
+/* Device scratch for a closure on an nx x ny x nz grid; 0 if unsupported. */
+size_t osb_closure_workspace_bytes(int nx, int ny, int nz);
+/* params_dev: caller-owned FP32 device array of 3 * osb_closure_param_count()
+ * values (parameters, then the two Adam moment arrays), 16-byte aligned.
+ * ws_dev: caller-owned, 256-byte aligned, osb_closure_workspace_bytes long.
+ * After writing parameters, call osb_closure_sync_weights. */
+osb_status osb_closure_create(int nx, int ny, int nz, float *params_dev, void *ws_dev, size_t ws_bytes,
+                              void *cuda_stream, osb_closure **out);
+osb_status osb_closure_destroy(osb_closure *closure);
+/* Per-channel input mean/std and output scale (arrays of 5; stds > 0). */
+osb_status osb_closure_set_normalization(osb_closure *closure, const float *in_mean, const float *in_std,
+                                         const float *out_std);
+/* Rebuilds the BF16 tensor-core weight layouts from the FP32 parameters. */
+osb_status osb_closure_sync_weights(osb_closure *closure);
+/* C_dev (device FP32, 5*N SoA) = out_std * net(normalised Q); Q_dev device
+ * FP64 fields with the given field stride (>= N).  Stream-ordered. */
+osb_status osb_closure_forward(osb_closure *closure, const double *Q_dev, size_t field_stride, float *C_dev);
+/* MSE between the normalised output for input X and the normalised target
+ * Cstar (both device FP64 fields, strides >= N); writes the loss (device FP32
+ * scalar) and the gradient of every parameter (device FP32, layout of the
+ * parameters; written, not accumulated).  Deterministic. */
+osb_status osb_closure_loss_grad(osb_closure *closure, const double *X_dev, size_t x_stride, const double *Cstar_dev,
+                                 size_t c_stride, float *grad_dev, float *loss_dev);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step >= 1)
+ * on the parameters with the given gradient, then osb_closure_sync_weights. */
+osb_status osb_closure_adam_step(osb_closure *closure, const float *grad_dev, float lr, int step);
+/* Attaches a closure to a grid of the same size (NULL detaches): every RK
+ * stage and osb_residual then add its correction to R.  Grids with a closure
+ * are stepped singly (osb_batch_step returns OSB_ERR_UNSUPPORTED). */
+osb_status osb_grid_set_closure(osb_grid *grid, osb_closure *closure);
+/* Box filter (training data for the closure): coarse = mean over factor^3
+ * blocks of a fine state.  Both device FP64, 5 fields, no padding; fine sizes
+ * multiples of factor.  Stream-ordered. */
+osb_status osb_box_filter(const double *fine_dev, int fnx, int fny, int fnz, int factor, double *coarse_dev,
+                          void *cuda_stream);
 
 /* Per-kernel timing (tooling, no counterpart in the paper).  profile_start
  * creates 4 CUDA events per stage for up to max_stages stage launches; each

@@ -49,6 +49,7 @@ struct osb_grid {
     char *batch_ctl;
     std::map<std::string, cudaGraphExec_t> *graphs;
     cudaStream_t capture_st;  // library-owned stream the batch graphs are captured on
+    osb_closure *closure;     // learned correction added to R in every stage, or nullptr
 };
 
 namespace {
@@ -405,6 +406,10 @@ osb_status osb_residual(osb_grid *g, double *R_dev) {
     a.src_stride = g->u_stride;
     a.R_out = R_dev;
     a.R_stride = g->d.n;
+    if (g->closure) {
+        cudaError_t ec = cl::closure_correction(g->closure, a.src, 1, a.src_stride, &a.closure);
+        if (ec != cudaSuccess) return cuda_fail(ec, "closure correction");
+    }
     cudaError_t e = g->K.residual(a);
     if (e != cudaSuccess) return cuda_fail(e, "residual");
     return OSB_OK;
@@ -466,6 +471,10 @@ static osb_status rk3_one_step(osb_grid *g) {
     if (s0 != OSB_OK) return s0;
     for (int k = 0; k < 3; ++k) {
         StageArgs a = stage_args(g, g->cur, k);
+        if (g->closure) {
+            cudaError_t e = cl::closure_correction(g->closure, a.src, a.src_is_f64, a.src_stride, &a.closure);
+            if (e != cudaSuccess) return cuda_fail(e, "closure correction");
+        }
         if (g->prof_ev && g->prof_used < g->prof_cap) {
             a.ev = g->prof_ev->data() + 4 * g->prof_used;
             g->prof_used += 1;
@@ -569,8 +578,10 @@ int tile_depth(const osb_grid_desc &d) {
 
 osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     if (!grids || n < 1 || n > MAXB || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "batch: need 1..128 grids, nsteps >= 0");
-    for (int i = 0; i < n; ++i)
+    for (int i = 0; i < n; ++i) {
         if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
+        if (grids[i]->closure) return fail(OSB_ERR_UNSUPPORTED, "batch: grids with a learned closure step singly");
+    }
     const osb_grid *g0 = grids[0];
     for (int i = 1; i < n; ++i) {
         const osb_grid *g = grids[i];
@@ -685,6 +696,13 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
 extern "C" {
 
 osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) { return batch_run(grids, n, nsteps); }
+
+osb_status osb_grid_set_closure(osb_grid *g, osb_closure *c) {
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    if (c && cl::closure_points(c) != g->d.n) return fail(OSB_ERR_INVALID_ARG, "closure grid size differs from the grid's");
+    g->closure = c;
+    return OSB_OK;
+}
 
 osb_status osb_batch_configure(double wait_limit_seconds, int test_stall) {
     if (!(wait_limit_seconds > 0) || wait_limit_seconds > 3600)

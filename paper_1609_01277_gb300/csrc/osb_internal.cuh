@@ -84,6 +84,7 @@ struct StageArgs {
     cudaStream_t stream;
     cudaEvent_t *ev;        // optional: 4 events recorded around the 3 kernels
     int zmarch;             // FP32 path: 1 = z-marching two-kernel stage, 0 = three-kernel stage
+    const float *closure;   // learned correction added to R (5 fields, stride d.n), or nullptr
 };
 
 // Kernel kinds reported by the profiling hooks.
@@ -127,6 +128,12 @@ struct BatchParams {
 };
 
 cudaError_t launch_batch(const BatchParams &P, int order, int precision, int visc_form, cudaStream_t st);
+
+// Learned closure (closure.cu).
+namespace cl {
+cudaError_t closure_correction(osb_closure *c, const void *src, int src_is_f64, size_t stride, const float **C);
+int closure_points(const osb_closure *c);
+}  // namespace cl
 
 // Host helpers shared by the translation units (defined in osb_api.cu).
 Phys make_phys(const osb_params &prm);

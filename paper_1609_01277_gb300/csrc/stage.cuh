@@ -291,6 +291,10 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
         res[4] = fma(T(a.ph.kappa), D2<R, 0, POL>(Tf, nb, c) + D2<R, 1, POL>(Tf, nb, c) + D2<R, 2, POL>(Tf, nb, c), res[4]);
     }
 
+    if (a.closure) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) res[m] += T(ld<POL, float>(a.closure + (size_t)m * a.d.n + i));
+    }
     if (MODE == 0) {
         T *qo = static_cast<T *>(a.q_out);
         if constexpr (sizeof(T) == 8) {

@@ -366,6 +366,10 @@ __global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a
                             sdx2<R>(S.der[DF_W], ce, c.d2[0]) + sdy2<R>(S.der[DF_W], ce, c.d2[1]));
         res[4] = fmaf(kap, sdx2<R>(S.der[DF_T], ce, c.d2[0]) + sdy2<R>(S.der[DF_T], ce, c.d2[1]) +
                                qd2<R>(qT, c.d2[2]), res[4]);
+        if (a.closure) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) res[m] += a.closure[(size_t)m * d.n + i];
+        }
         if (active) {
 #pragma unroll
             for (int m = 0; m < 5; ++m) {

@@ -1,0 +1,128 @@
+"""Learned closure on the GPU against the CPU network oracle, through the C
+ABI: forward, loss and parameter gradients, Adam, box filter, the correction
+added to R, and what training gains over the solver without it.
+
+Tolerances: BF16 operands (unit roundoff 2^-9) with FP32 accumulation on the
+GPU vs float64 sums on the CPU; an element whose pre-activation sits at a BF16
+rounding boundary can round differently, so outputs and gradients are held
+to a relative L2 of 1e-2 (loss 1e-3)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import closure_oracle as co
+from oracle import oracle as orc
+from paper_1609_01277_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mods():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_01277_gb300 import build
+    build.build()
+    from paper_1609_01277_gb300 import closure, osb
+    osb.load()
+    return osb, closure, torch
+
+
+def _setup(mods, n=(16, 8, 8), seed=0):
+    osb, closure, torch = mods
+    nx, ny, nz = n
+    rng = np.random.Generator(np.random.PCG64(seed))
+    theta = (closure.init_params(seed) + rng.standard_normal(co.param_count()).astype(np.float32) * 0.02)
+    theta = theta.astype(np.float32)
+    Q = np.stack([1 + 0.2 * inputs.smooth_field(nx, ny, nz, seed + i) for i in range(5)])
+    C = np.stack([inputs.smooth_field(nx, ny, nz, seed + 10 + i) for i in range(5)])
+    mean, std, out = np.array([1.0, 0.9, 1.1, 1.0, 1.05]), np.array([0.2, 0.25, 0.2, 0.3, 0.2]), np.array(
+        [0.5, 1.0, 2.0, 0.7, 1.5])
+    c = closure.Closure(nx, ny, nz, params=theta)
+    c.set_normalization(mean, std, out)
+    return c, theta, Q, C, mean, std, out
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
+
+
+def test_forward_matches_oracle(mods):
+    osb, closure, torch = mods
+    c, theta, Q, _, mean, std, out = _setup(mods)
+    Cg = c.forward(torch.from_numpy(Q).cuda()).cpu().numpy()
+    Co = co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16")
+    assert _rel(Cg, Co) < 1e-2
+
+
+def test_loss_and_gradients_match_oracle(mods):
+    osb, closure, torch = mods
+    c, theta, Q, C, mean, std, out = _setup(mods, n=(16, 8, 12), seed=3)
+    loss, grad = c.loss_grad(torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda())
+    lo, go = co.loss_grad(theta.astype(np.float64), Q, C, mean, std, out, mode="bf16")
+    assert float(loss.item()) == pytest.approx(lo, rel=1e-3)
+    g = grad.cpu().numpy().astype(np.float64)
+    P, Po = co.unpack(g), co.unpack(go)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert _rel(P[name], Po[name]) < 2e-2, name
+
+
+def test_adam_step_matches_formula(mods):
+    osb, closure, torch = mods
+    c, theta, Q, C, *_ = _setup(mods, seed=5)
+    Qd, Cd = torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda()
+    _, grad = c.loss_grad(Qd, Cd)
+    g = grad.cpu().numpy().astype(np.float64)
+    c.train_step(Qd, Cd, 1e-3)
+    th, _, _ = co.adam(theta.astype(np.float64), np.zeros_like(g), np.zeros_like(g), g, 1e-3, 1)
+    assert np.allclose(c.get_params(), th, rtol=1e-5, atol=1e-7)
+
+
+def test_box_filter_matches_oracle(mods):
+    osb, closure, torch = mods
+    rng = np.random.Generator(np.random.PCG64(4))
+    Q = rng.standard_normal((5, 16, 8, 24))
+    F = closure.box_filter(torch.from_numpy(Q).cuda(), (24, 8, 16), 4).cpu().numpy()
+    assert np.allclose(F, co.box_filter(Q, 4), rtol=1e-14, atol=1e-15)
+
+
+def test_attached_closure_adds_correction_to_residual(mods):
+    osb, closure, torch = mods
+    n = 16
+    c, *_ = _setup(mods, n=(n, n, n), seed=7)
+    g = osb.Grid(osb.Config(n, n, n, order=4, dt=1e-3))
+    g.init_taylor_green(inputs.gaussian_noise(n, n, n, 1), 1e-2)
+    R0 = g.residual().cpu().numpy()
+    Cg = c.forward(g.get_state_device()).cpu().numpy().astype(np.float64)
+    c.attach(g)
+    R1 = g.residual().cpu().numpy()
+    assert np.allclose(R1 - R0, Cg, rtol=1e-6, atol=1e-12 * np.abs(R0).max())
+    # stepping with the closure differs; detaching restores the plain solver bitwise
+    g.step(2)
+    closure.Closure.detach(g)
+    p = osb.Grid(osb.Config(n, n, n, order=4, dt=1e-3))
+    p.set_state(g.get_state())
+    q = osb.Grid(osb.Config(n, n, n, order=4, dt=1e-3))
+    q.set_state(g.get_state())
+    p.step(3)
+    q.step(3)
+    assert np.array_equal(p.get_state(), q.get_state())
+
+
+def test_training_reduces_a_priori_error(mods):
+    """Closure data from the solver (fine 64^3 -> coarse 16^3, factor 4): after
+    training, the closure explains part of the commutation residual on held-out
+    snapshots, which the plain coarse solver misses entirely (error 1)."""
+    osb, closure, torch = mods
+    data = closure.make_training_data(64, 4, snapshots=12, every=25, Re=400.0)
+    c = closure.Closure(16, 16, 16, seed=0)
+    c.set_normalization(*closure.normalisation(data))
+    train_idx, test_idx = list(range(0, 12, 3)) + list(range(1, 12, 3)), list(range(2, 12, 3))
+    base = closure.a_priori_error(None, data, test_idx)
+    hist = closure.train(c, data, epochs=25, lr=2e-3, train_idx=train_idx)
+    after = closure.a_priori_error(c, data, test_idx)
+    assert base == pytest.approx(1.0)
+    assert hist[-1] < 0.5 * hist[0]
+    assert after < 0.8, (after, hist[:3], hist[-3:])
