@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--ensemble-steps", type=int, default=5)
+    ap.add_argument("--no-closure", action="store_true")
     return ap.parse_args()
 
 
@@ -416,6 +417,22 @@ def run_ours(args):
         e64, e32 = variants["ensemble64_order4_fp64"], variants["ensemble64_order4_fp32"]
         e32["speedup_vs_fp64_ensemble"] = e32["value"] / e64["value"]
         e32["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(e32["ke_first4"], e64["ke_first4"]))
+
+    if not args.no_closure and world == 1:
+        from paper_1609_01277_gb300 import closure as clo
+        r = clo.run_experiment(n_fine=128, factor=4, t_end=4.0, snap_every=48, epochs=20)
+        keep = {k: v for k, v in r.items() if k != "curves"}
+        best = r["closure"]["momentum_half"]
+        keep["summary"] = {
+            "judge": "KE of the box-filtered 128^3 run on the 32^3 grid",
+            "ke_err_plain_32": r["plain"]["ke_err_vs_filtered_fine"],
+            "ke_err_closure_32": best["ke_err_vs_filtered_fine"],
+            "dissipation_err_plain_32": r["plain"]["dissipation_err"],
+            "dissipation_err_closure_32": best["dissipation_err"],
+            "closure_cost_vs_plain_32": best["seconds"] / r["plain"]["seconds"],
+            "speedup_vs_filtered_fine_run": r["seconds"]["fine_data"] / best["seconds"],
+            "fallback_t": best["fallback_t"]}
+        variants["closure_tgv128to32"] = keep
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

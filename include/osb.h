@@ -234,6 +234,11 @@ osb_status osb_closure_destroy(osb_closure *closure);
 /* Per-channel input mean/std and output scale (arrays of 5; stds > 0). */
 osb_status osb_closure_set_normalization(osb_closure *closure, const float *in_mean, const float *in_std,
                                          const float *out_std);
+/* Which equations receive the correction (apply[5], nonzero = yes; default all
+ * five).  Training always fits all five outputs; the mask only selects what
+ * is added to R.  Correcting only the momentum equations (1,1,1 for rho u_i,
+ * 0 for rho and rho E) plays the role of a subgrid-stress model. */
+osb_status osb_closure_set_channels(osb_closure *closure, const int *apply);
 /* Rebuilds the BF16 tensor-core weight layouts from the FP32 parameters. */
 osb_status osb_closure_sync_weights(osb_closure *closure);
 /* C_dev (device FP32, 5*N SoA) = out_std * net(normalised Q); Q_dev device

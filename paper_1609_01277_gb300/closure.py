@@ -33,13 +33,14 @@ def _declare():
     L.osb_closure_destroy.argtypes = [vp]
     L.osb_closure_set_normalization.argtypes = [vp, fp, fp, fp]
     L.osb_closure_sync_weights.argtypes = [vp]
+    L.osb_closure_set_channels.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.osb_closure_forward.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.osb_closure_loss_grad.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp, vp]
     L.osb_closure_adam_step.argtypes = [vp, vp, ctypes.c_float, ctypes.c_int]
     L.osb_grid_set_closure.argtypes = [vp, vp]
     L.osb_box_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     for name in ("osb_closure_create", "osb_closure_destroy", "osb_closure_set_normalization",
-                 "osb_closure_sync_weights", "osb_closure_forward", "osb_closure_loss_grad",
+                 "osb_closure_sync_weights", "osb_closure_set_channels", "osb_closure_forward", "osb_closure_loss_grad",
                  "osb_closure_adam_step", "osb_grid_set_closure", "osb_box_filter"):
         getattr(L, name).restype = ctypes.c_int
     L._closure_declared = True
@@ -113,6 +114,10 @@ class Closure:
         self.norm = (np.asarray(in_mean, float), np.asarray(in_std, float), np.asarray(out_std, float))
         check(_declare().osb_closure_set_normalization(self.handle, f(in_mean), f(in_std), f(out_std)),
               "osb_closure_set_normalization")
+
+    def set_channels(self, apply) -> None:
+        arr = (ctypes.c_int * 5)(*[int(bool(v)) for v in apply])
+        check(_declare().osb_closure_set_channels(self.handle, arr), "osb_closure_set_channels")
 
     def forward(self, Q_dev):
         """Correction C (5, nz, ny, nx) FP32 for a device FP64 state (5, nz, ny, nx)."""
@@ -224,3 +229,157 @@ def a_priori_error(closure: Closure | None, data, idx):
         num += float((Y - C).norm())
         den += float(Y.norm())
     return num / den
+
+
+def _ke_run(grid, X0, steps_per_sample, samples, closure=None, history=4):
+    """KE of a coarse run every steps_per_sample steps (from state X0).
+
+    With a closure attached, the plain solver is the fallback: when a sample
+    shows the signs that precede a blow-up -- a non-finite state, kinetic energy
+    above 1.01 E_k(0) (the decaying Taylor-Green flow never gains energy), or a
+    Courant number above twice its initial value -- the run returns to the
+    oldest of the last `history` good samples, detaches the closure and
+    continues from there with the plain solver.
+    Returns (ke, seconds, fallback_time or None)."""
+    import time
+
+    import torch
+    grid.set_state_device(X0)
+    if closure is not None:
+        closure.attach(grid)
+    d0 = grid.diagnostics()
+    ke = [d0["ke"]]
+    hist = [(0, grid.get_state_device().clone())] if closure is not None else []
+    fallback_t = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = 0
+    while s < samples - 1:
+        grid.step(steps_per_sample)
+        s += 1
+        d = grid.diagnostics(raise_nonfinite=False)
+        if closure is not None and fallback_t is None:
+            if (d["status"] != 0 or not np.isfinite(d["ke"]) or d["ke"] > 1.01 * d0["ke"]
+                    or not d["max_cfl"] < 2.0 * d0["max_cfl"]):
+                s0, good = hist[0]
+                fallback_t = s0 * steps_per_sample * grid.cfg.dt
+                Closure.detach(grid)
+                grid.set_state_device(good)
+                del ke[s0 + 1:]
+                s = s0
+                continue
+            hist.append((s, grid.get_state_device().clone()))
+            if len(hist) > history:
+                hist.pop(0)
+        ke.append(d["ke"])
+    el = time.perf_counter() - t0
+    if closure is not None and fallback_t is None:
+        Closure.detach(grid)
+    return np.array(ke), el, fallback_t
+
+
+def run_experiment(n_fine=256, factor=4, t_end=10.0, snap_every=48, epochs=20, lr=1e-3, Re=1600.0, order=4,
+                   seed=0):
+    """Fine run -> filtered training data -> training -> a-posteriori KE-decay
+    comparison of the coarse grid with and without the closure (and the plain
+    solver at twice the coarse resolution), against the filtered fine run."""
+    import time
+
+    import torch
+    n_c = n_fine // factor
+    dt_f = 3.385e-3 * 64.0 / n_fine
+    samples = int(round(t_end / (snap_every * dt_f))) + 1
+    t0 = time.perf_counter()
+    data = make_training_data(n_fine, factor, samples, snap_every, order=order, Re=Re, dt_fine=dt_f)
+    t_data = time.perf_counter() - t0
+    times = np.array(data["t"])
+    # judge: KE of the filtered fine state (coarse-grid diagnostics)
+    judge = osb.Grid(osb.Config(n_c, n_c, n_c, order=order, Re=Re, dt=dt_f * factor))
+    ke_ref = []
+    for X in data["X"]:
+        judge.set_state_device(X)
+        ke_ref.append(judge.diagnostics()["ke"])
+    ke_ref = np.array(ke_ref)
+    ke_fine = np.array(data["ke_fine"])
+    # training on 3 of every 4 snapshots
+    train_idx = [i for i in range(samples) if i % 4 != 3]
+    test_idx = [i for i in range(samples) if i % 4 == 3]
+    c = Closure(n_c, n_c, n_c, seed=seed)
+    c.set_normalization(*normalisation(data))
+    t0 = time.perf_counter()
+    hist = train(c, data, epochs, lr=lr, train_idx=train_idx, seed=seed)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    apriori = dict(plain=a_priori_error(None, data, test_idx), closure=a_priori_error(c, data, test_idx))
+    # a posteriori: coarse runs from the filtered initial state
+    cstep = snap_every // factor
+    g = osb.Grid(osb.Config(n_c, n_c, n_c, order=order, Re=Re, dt=dt_f * factor))
+    ke_plain, t_plain, _ = _ke_run(g, data["X"][0], cstep, samples)
+    gains = {}
+    in_mean, in_std, out_std = c.norm
+    for label, apply, gain in (("momentum", (0, 1, 1, 1, 0), 1.0), ("momentum_half", (0, 1, 1, 1, 0), 0.5),
+                               ("all", (1, 1, 1, 1, 1), 1.0)):
+        c.set_channels(apply)
+        c.set_normalization(in_mean, in_std, out_std * gain)
+        gains[label] = _ke_run(g, data["X"][0], cstep, samples, closure=c)
+    # default for later use: momentum equations only, half gain
+    c.set_normalization(in_mean, in_std, out_std * 0.5)
+    c.set_channels((0, 1, 1, 1, 0))
+    # plain solver at twice the coarse resolution, started from the factor/2 filtered fine state
+    n2 = 2 * n_c
+    g2 = osb.Grid(osb.Config(n2, n2, n2, order=order, Re=Re, dt=dt_f * factor / 2))
+    fine0 = osb.Grid(osb.Config(n_fine, n_fine, n_fine, order=order, Re=Re, dt=dt_f))
+    from . import inputs
+    fine0.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n_fine, n_fine, n_fine, 1234)).cuda(), 1e-4)
+    X2 = box_filter(fine0.get_state_device(), (n_fine,) * 3, factor // 2)
+    del fine0
+    ke_2x, t_2x, _ = _ke_run(g2, X2, 2 * cstep, samples)
+
+    def err(ke, ref):
+        return float(np.max(np.abs(ke - ref)) / ref[0])
+
+    def eps(ke):
+        return -np.gradient(ke, times)
+
+    def eps_err(ke, ref):
+        e, r = eps(ke), eps(ref)
+        return float(np.max(np.abs(e - r)) / np.max(np.abs(r)))
+
+    res = dict(n_fine=n_fine, factor=factor, n_coarse=n_c, t_end=float(times[-1]), samples=samples,
+               snap_every_fine_steps=snap_every, epochs=epochs, train_snapshots=len(train_idx),
+               loss_first=hist[0], loss_last=hist[-1], a_priori_rel_err=apriori,
+               plain=dict(ke_err_vs_filtered_fine=err(ke_plain, ke_ref), ke_err_vs_fine=err(ke_plain, ke_fine),
+                          dissipation_err=eps_err(ke_plain, ke_ref), seconds=t_plain),
+               plain_2x=dict(ke_err_vs_filtered_fine=err(ke_2x, ke_ref), ke_err_vs_fine=err(ke_2x, ke_fine),
+                             dissipation_err=eps_err(ke_2x, ke_ref), seconds=t_2x),
+               closure={label: dict(ke_err_vs_filtered_fine=err(v[0], ke_ref), ke_err_vs_fine=err(v[0], ke_fine),
+                                        dissipation_err=eps_err(v[0], ke_ref), seconds=v[1], fallback_t=v[2])
+                        for label, v in gains.items()},
+               seconds=dict(fine_data=t_data, train=t_train),
+               curves=dict(t=times.tolist(), ke_filtered_fine=ke_ref.tolist(), ke_fine=ke_fine.tolist(),
+                           ke_plain=ke_plain.tolist(), ke_plain_2x=ke_2x.tolist(),
+                           **{f"ke_closure_{label}": v[0].tolist() for label, v in gains.items()}))
+    return res
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="learned-closure experiment on the Taylor-Green vortex")
+    ap.add_argument("--fine", type=int, default=256)
+    ap.add_argument("--factor", type=int, default=4)
+    ap.add_argument("--t-end", type=float, default=10.0)
+    ap.add_argument("--snap-every", type=int, default=48)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    from . import build
+    build.build()
+    osb.load()
+    r = run_experiment(a.fine, a.factor, a.t_end, a.snap_every, a.epochs, a.lr)
+    if a.out:
+        with open(a.out, "w") as f:
+            json.dump(r, f)
+    print(json.dumps({k: v for k, v in r.items() if k != "curves"}))

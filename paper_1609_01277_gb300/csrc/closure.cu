@@ -342,11 +342,11 @@ __global__ void k_sum_partials(const float *__restrict__ partial, int nparts, fl
     }
 }
 
-// Correction added to R: C_m(p) = out_std_m * y[p][m], in SoA (stride n).
+// Correction added to R: C_m(p) = apply_m * out_std_m * y[p][m], in SoA (stride n).
 __global__ void k_closure_out(int n, const float *__restrict__ y, const float *__restrict__ nrm, float *__restrict__ C) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
 #pragma unroll
-        for (int c = 0; c < 5; ++c) C[(size_t)c * n + p] = nrm[10 + c] * y[(size_t)p * 8 + c];
+        for (int c = 0; c < 5; ++c) C[(size_t)c * n + p] = nrm[16 + c] * nrm[10 + c] * y[(size_t)p * 8 + c];
 }
 
 // FP32 master parameters -> BF16 forward weights Wf[k][co][ci] (padded) and
@@ -435,7 +435,7 @@ size_t carve(char *base, int n, Buffers *B) {
     b.C = (float *)take((size_t)n * 5 * 4);
     b.part = (float *)take((size_t)NPART * wgrad_stride<32, 32>() * 4);
     b.lpart = (float *)take(NPART * 4);
-    b.nrm = (float *)take(16 * 4);
+    b.nrm = (float *)take(24 * 4);  // mean[5], 1/std[5], out_std[5], -, apply[5]
     b.b3pad = (float *)take(8 * 4);
     b.wf1 = (uint16_t *)take(27 * H * 16 * 2);
     b.wf2 = (uint16_t *)take(27 * H * H * 2);
@@ -477,7 +477,7 @@ struct osb_closure {
     char *ws;
     osb::cl::Buffers B;
     cudaStream_t st;
-    float nrm_h[16];
+    float nrm_h[24];
 };
 
 namespace osb {
@@ -551,7 +551,7 @@ osb_status osb_closure_create(int nx, int ny, int nz, float *params_dev, void *w
     c->ws = (char *)ws_dev;
     c->st = (cudaStream_t)stream;
     cl::carve(c->ws, c->n, &c->B);
-    for (int i = 0; i < 16; ++i) c->nrm_h[i] = (i >= 5 && i < 15) ? 1.f : 0.f;
+    for (int i = 0; i < 24; ++i) c->nrm_h[i] = ((i >= 5 && i < 15) || (i >= 16 && i < 21)) ? 1.f : 0.f;
     // zero the padded BF16 weight buffers once (padding entries stay zero)
     cudaError_t e = cudaMemsetAsync(c->B.wf1, 0, (char *)c->ws + need - (char *)c->B.wf1, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->B.nrm, c->nrm_h, sizeof(c->nrm_h), cudaMemcpyHostToDevice, c->st);
@@ -587,6 +587,18 @@ osb_status osb_closure_set_normalization(osb_closure *c, const float *in_mean, c
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
         set_last_error("closure: normalisation copy failed");
+        return OSB_ERR_CUDA;
+    }
+    return OSB_OK;
+}
+
+osb_status osb_closure_set_channels(osb_closure *c, const int *apply) {
+    if (!c || !apply) return OSB_ERR_INVALID_ARG;
+    for (int i = 0; i < 5; ++i) c->nrm_h[16 + i] = apply[i] ? 1.f : 0.f;
+    cudaError_t e = cudaMemcpyAsync(c->B.nrm, c->nrm_h, sizeof(c->nrm_h), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        set_last_error("closure: channel mask copy failed");
         return OSB_ERR_CUDA;
     }
     return OSB_OK;

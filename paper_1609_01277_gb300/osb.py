@@ -27,7 +27,11 @@ STATUS = {0: "OSB_OK", 1: "OSB_ERR_INVALID_ARG", 2: "OSB_ERR_UNSUPPORTED", 3: "O
 EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_grid_destroy",
            "osb_init_taylor_green", "osb_set_state", "osb_get_state", "osb_set_state_device",
            "osb_get_state_device", "osb_residual", "osb_rk3_step", "osb_diagnostics",
-           "osb_batch_step", "osb_batch_configure", "osb_autotune", "osb_diagnostics_noalloc", "osb_profile_start", "osb_profile_stop",
+           "osb_batch_step", "osb_batch_configure", "osb_autotune", "osb_diagnostics_noalloc",
+           "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_closure_create", "osb_closure_destroy",
+           "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_sync_weights",
+           "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
+           "osb_box_filter", "osb_profile_start", "osb_profile_stop",
            "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
@@ -92,7 +96,8 @@ def load(path: str | None = None):
     L.osb_status_string.restype = ctypes.c_char_p
     L.osb_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("osb_state_bytes", "osb_workspace_bytes", "osb_status_string", "osb_last_error"):
+        if name not in ("osb_state_bytes", "osb_workspace_bytes", "osb_status_string", "osb_last_error",
+                        "osb_closure_param_count", "osb_closure_workspace_bytes"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
