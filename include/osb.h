@@ -253,6 +253,9 @@ osb_status osb_closure_loss_grad(osb_closure *closure, const double *X_dev, size
 /* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected, step >= 1)
  * on the parameters with the given gradient, then osb_closure_sync_weights. */
 osb_status osb_closure_adam_step(osb_closure *closure, const float *grad_dev, float lr, int step);
+/* Synchronises the closure's stream and reports OSB_ERR_TIMEOUT if a bounded
+ * wait of a tensor-core convolution ever ran out (results then invalid). */
+osb_status osb_closure_status(osb_closure *closure);
 /* Attaches a closure to a grid of the same size (NULL detaches): every RK
  * stage and osb_residual then add its correction to R.  Grids with a closure
  * are stepped singly (osb_batch_step returns OSB_ERR_UNSUPPORTED). */

@@ -34,13 +34,14 @@ def _declare():
     L.osb_closure_set_normalization.argtypes = [vp, fp, fp, fp]
     L.osb_closure_sync_weights.argtypes = [vp]
     L.osb_closure_set_channels.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.osb_closure_status.argtypes = [vp]
     L.osb_closure_forward.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.osb_closure_loss_grad.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp, vp]
     L.osb_closure_adam_step.argtypes = [vp, vp, ctypes.c_float, ctypes.c_int]
     L.osb_grid_set_closure.argtypes = [vp, vp]
     L.osb_box_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     for name in ("osb_closure_create", "osb_closure_destroy", "osb_closure_set_normalization",
-                 "osb_closure_sync_weights", "osb_closure_set_channels", "osb_closure_forward", "osb_closure_loss_grad",
+                 "osb_closure_sync_weights", "osb_closure_set_channels", "osb_closure_status", "osb_closure_forward", "osb_closure_loss_grad",
                  "osb_closure_adam_step", "osb_grid_set_closure", "osb_box_filter"):
         getattr(L, name).restype = ctypes.c_int
     L._closure_declared = True
@@ -114,6 +115,9 @@ class Closure:
         self.norm = (np.asarray(in_mean, float), np.asarray(in_std, float), np.asarray(out_std, float))
         check(_declare().osb_closure_set_normalization(self.handle, f(in_mean), f(in_std), f(out_std)),
               "osb_closure_set_normalization")
+
+    def status(self) -> None:
+        check(_declare().osb_closure_status(self.handle), "osb_closure_status")
 
     def set_channels(self, apply) -> None:
         arr = (ctypes.c_int * 5)(*[int(bool(v)) for v in apply])

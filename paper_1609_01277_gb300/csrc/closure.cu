@@ -12,6 +12,8 @@
 // training data), and the per-channel normalisation of inputs and targets.
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <new>
 
@@ -142,6 +144,175 @@ __global__ void __launch_bounds__(256) k_conv(int nx, int ny, int nz, const uint
             *reinterpret_cast<uint32_t *>(o + gp1 * CO + c0) = (uint32_t)bf16_bits(v[2]) | ((uint32_t)bf16_bits(v[3]) << 16);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same convolution on the 5th-generation tensor cores (tcgen05): one CTA
+// of 128 threads per brick of 8 x 16 x 1 points (M = 128 rows of the GEMM),
+// N = CO = 32 output channels, K = 27 taps x CI.  Operands in shared memory in
+// the K-major, no-swizzle core-matrix layout (8 rows x 16 bytes):
+//   A (input halo 10 x 18 x 3): [CI/8 chunks][540 positions][8 ch]; the 8 rows
+//     of a core matrix are 8 consecutive x positions of one halo row, so for a
+//     tap the descriptor strides are constant: 160 B between core matrices along
+//     M (next y row), 8640 B along K (next channel chunk);
+//   B (weights): [27 taps][CI/8 chunks][CO][8 ch]; 128 B along N, CO*16 B along K.
+// One thread issues the 27*CI/16 MMAs into an FP32 accumulator of 32 TMEM
+// columns; tcgen05.commit signals an mbarrier; each warp then reads its 32
+// rows (points) with tcgen05.ld and applies the epilogue.
+// ---------------------------------------------------------------------------
+constexpr int TBX = 8, TBY = 16, THX = TBX + 2, THY = TBY + 2, THZ = 3, THN = THX * THY * THZ;  // 540
+constexpr unsigned TC_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3fffu) | ((uint64_t)((lbo >> 4) & 0x3fffu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3fffu) << 32) | (1ull << 46);
+}
+
+template <int CO>
+__host__ __device__ constexpr uint32_t tc_idesc() {
+    // D FP32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1), both K-major,
+    // N >> 3 at bits 17-22, M >> 4 at bits 24-28 (M = 128)
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CO >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int CI, int CO>
+constexpr size_t tc_smem_used() {
+    return (size_t)THN * CI * 2 + (size_t)27 * CI * CO * 2;
+}
+
+template <int CI, int CO, int EPI>
+__global__ void __launch_bounds__(128) k_conv_tc(int nx, int ny, int nz, const uint16_t *__restrict__ in,
+                                                 const uint16_t *__restrict__ W, const float *__restrict__ bias,
+                                                 const uint16_t *__restrict__ mask, void *__restrict__ out,
+                                                 int *__restrict__ err) {
+    static_assert(CO == 32, "tensor-core path built for 32 output channels");
+    constexpr int NCH = CI / 8;
+    extern __shared__ __align__(128) uint8_t tsm[];
+    uint8_t *A = tsm;
+    uint8_t *B = tsm + THN * CI * 2;
+    __shared__ uint32_t taddr_s;
+    __shared__ __align__(8) uint64_t bar;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bx = nx / TBX, by = ny / TBY;
+    const int brick = blockIdx.x;
+    const int x0 = (brick % bx) * TBX, y0 = ((brick / bx) % by) * TBY, z0 = brick / (bx * by);
+
+    if (warp == 0) {
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&taddr_s);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(sa));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    const uint32_t bar_a = (uint32_t)__cvta_generic_to_shared(&bar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // halo tile -> A (chunk-major core-matrix rows of 16 bytes)
+    for (int e = tid; e < THN * NCH; e += 128) {
+        const int pos = e / NCH, ch = e - pos * NCH;
+        const int hx = pos % THX, hy = (pos / THX) % THY, hz = pos / (THX * THY);
+        const int gx = wrapi(x0 + hx - 1, nx), gy = wrapi(y0 + hy - 1, ny), gz = wrapi(z0 + hz - 1, nz);
+        const size_t gp = ((size_t)gz * ny + gy) * nx + gx;
+        *reinterpret_cast<uint4 *>(A + ((size_t)ch * THN + pos) * 16) =
+            *reinterpret_cast<const uint4 *>(in + gp * CI + ch * 8);
+    }
+    // weights [27][CO][CI] -> B [27][NCH][CO][8]
+    for (int e = tid; e < 27 * CO * NCH; e += 128) {
+        const int k = e / (CO * NCH), n = (e / NCH) % CO, ch = e % NCH;
+        *reinterpret_cast<uint4 *>(B + (((size_t)k * NCH + ch) * CO + n) * 16) =
+            *reinterpret_cast<const uint4 *>(W + ((size_t)k * CO + n) * CI + ch * 8);
+    }
+    // make the generic-proxy shared-memory writes visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = taddr_s;
+
+    if (tid == 0) {
+        const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(A), b0 = (uint32_t)__cvta_generic_to_shared(B);
+        constexpr uint32_t idesc = tc_idesc<CO>();
+        for (int k = 0; k < 27; ++k) {
+            const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;  // halo offsets of brick point (0, 0)
+            const uint32_t pos0 = (uint32_t)((dz * THY + dy) * THX + dx);
+#pragma unroll
+            for (int s = 0; s < CI / 16; ++s) {
+                const uint64_t ad = tc_desc(a0 + ((uint32_t)(2 * s) * THN + pos0) * 16, THN * 16, THX * 16);
+                const uint64_t bd = tc_desc(b0 + ((uint32_t)(k * NCH + 2 * s) * CO) * 16, CO * 16, 128);
+                const uint32_t acc = (k | s) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+                     : "memory");
+    }
+    // bounded wait for the accumulator (phase 0 of the mbarrier)
+    {
+        uint32_t done = 0;
+        for (unsigned it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done)
+                : "r"(bar_a), "r"(0u)
+                : "memory");
+            if (!done) __nanosleep(64);
+        }
+        if (!done && lane == 0) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+
+    // epilogue: this thread's point is row 32*warp + lane of the brick
+    const int p = warp * 32 + lane, px = p % TBX, py = p / TBX;
+    const size_t gp = ((size_t)z0 * ny + (y0 + py)) * nx + (x0 + px);
+    float v[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) v[c] = __uint_as_float(r[c]);
+    if (EPI != EPI_MASK) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] += bias[c];
+    }
+    if (EPI == EPI_RELU) {
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = fmaxf(v[c], 0.f);
+    }
+    if (EPI == EPI_MASK) {
+        const uint4 *mk = reinterpret_cast<const uint4 *>(mask + gp * CO);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint4 m4 = mk[q];
+            const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+            for (int h = 0; h < 8; ++h) {
+                const uint16_t mb = (uint16_t)(mw[h / 2] >> (16 * (h & 1)));
+                if (!(bf16_val(mb) > 0.f)) v[q * 8 + h] = 0.f;
+            }
+        }
+    }
+    uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(out) + gp * CO);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h)
+            w[h] = (uint32_t)bf16_bits(v[q * 8 + 2 * h]) | ((uint32_t)bf16_bits(v[q * 8 + 2 * h + 1]) << 16);
+        o[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr));
 }
 
 template <int CI, int CO>
@@ -410,6 +581,7 @@ constexpr int NPART = 152 * 2;  // weight-gradient partials (CTAs of k_wgrad)
 struct Buffers {
     uint16_t *x0, *h1, *h2, *dy, *dz2, *dz1;
     float *y, *t, *C, *part, *lpart, *nrm, *b3pad;
+    int *tcerr;  // set when a tensor-core accumulator wait ran out
     uint16_t *wf1, *wf2, *wf3, *wd2, *wd3;
 };
 
@@ -437,6 +609,7 @@ size_t carve(char *base, int n, Buffers *B) {
     b.lpart = (float *)take(NPART * 4);
     b.nrm = (float *)take(24 * 4);  // mean[5], 1/std[5], out_std[5], -, apply[5]
     b.b3pad = (float *)take(8 * 4);
+    b.tcerr = (int *)take(16);
     b.wf1 = (uint16_t *)take(27 * H * 16 * 2);
     b.wf2 = (uint16_t *)take(27 * H * H * 2);
     b.wf3 = (uint16_t *)take(27 * 8 * H * 2);
@@ -446,9 +619,27 @@ size_t carve(char *base, int n, Buffers *B) {
     return off;
 }
 
+
+int g_tc_mode = -1;  // 1: tensor-core (tcgen05) convolutions where applicable, 0: mma.sync only
+
 template <int CI, int CO, int EPI>
 cudaError_t conv(int nx, int ny, int nz, const uint16_t *in, const uint16_t *W, const float *bias, const uint16_t *mask,
-                 void *out, cudaStream_t st) {
+                 void *out, int *tcerr, cudaStream_t st) {
+    {
+        const char *env = getenv("OSB_CLOSURE_MMA");
+        g_tc_mode = !(env && strcmp(env, "sync") == 0);
+    }
+    if constexpr (CO == 32 && EPI != EPI_LIN) {
+        if (g_tc_mode && ny % TBY == 0 && nx % TBX == 0 && tcerr) {
+            constexpr size_t sm = tc_smem_used<CI, CO>();
+            cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)sm);
+            if (e != cudaSuccess) return e;
+            const int bricks = (nx / TBX) * (ny / TBY) * nz;
+            k_conv_tc<CI, CO, EPI><<<bricks, 128, sm, st>>>(nx, ny, nz, in, W, bias, mask, out, tcerr);
+            return cudaGetLastError();
+        }
+    }
     const size_t sm = conv_smem<CI, CO>();
     cudaError_t e = cudaFuncSetAttribute(k_conv<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -491,11 +682,13 @@ cudaError_t forward_y(osb_closure *c, const void *src, int src_is_f64, size_t st
         k_features<double><<<blocks, 256, 0, c->st>>>(n, (const double *)src, stride, c->B.nrm, c->B.x0);
     else
         k_features<float><<<blocks, 256, 0, c->st>>>(n, (const float *)src, stride, c->B.nrm, c->B.x0);
-    cudaError_t e = conv<16, 32, EPI_RELU>(c->nx, c->ny, c->nz, c->B.x0, c->B.wf1, c->params + OFF_B1, nullptr, c->B.h1, c->st);
+    cudaError_t e = conv<16, 32, EPI_RELU>(c->nx, c->ny, c->nz, c->B.x0, c->B.wf1, c->params + OFF_B1, nullptr, c->B.h1,
+                                           c->B.tcerr, c->st);
     if (e != cudaSuccess) return e;
-    e = conv<32, 32, EPI_RELU>(c->nx, c->ny, c->nz, c->B.h1, c->B.wf2, c->params + OFF_B2, nullptr, c->B.h2, c->st);
+    e = conv<32, 32, EPI_RELU>(c->nx, c->ny, c->nz, c->B.h1, c->B.wf2, c->params + OFF_B2, nullptr, c->B.h2, c->B.tcerr,
+                               c->st);
     if (e != cudaSuccess) return e;
-    return conv<32, 8, EPI_LIN>(c->nx, c->ny, c->nz, c->B.h2, c->B.wf3, c->B.b3pad, nullptr, c->B.y, c->st);
+    return conv<32, 8, EPI_LIN>(c->nx, c->ny, c->nz, c->B.h2, c->B.wf3, c->B.b3pad, nullptr, c->B.y, c->B.tcerr, c->st);
 }
 
 cudaError_t closure_correction(osb_closure *c, const void *src, int src_is_f64, size_t stride, const float **C) {
@@ -553,7 +746,7 @@ osb_status osb_closure_create(int nx, int ny, int nz, float *params_dev, void *w
     cl::carve(c->ws, c->n, &c->B);
     for (int i = 0; i < 24; ++i) c->nrm_h[i] = ((i >= 5 && i < 15) || (i >= 16 && i < 21)) ? 1.f : 0.f;
     // zero the padded BF16 weight buffers once (padding entries stay zero)
-    cudaError_t e = cudaMemsetAsync(c->B.wf1, 0, (char *)c->ws + need - (char *)c->B.wf1, c->st);
+    cudaError_t e = cudaMemsetAsync(c->B.tcerr, 0, (char *)c->ws + need - (char *)c->B.tcerr, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->B.nrm, c->nrm_h, sizeof(c->nrm_h), cudaMemcpyHostToDevice, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
@@ -649,11 +842,13 @@ osb_status osb_closure_loss_grad(osb_closure *c, const double *X_dev, size_t xs,
     // layer 3: dW3, db3; then dz2 = (W3^T dy) * [h2 > 0]
     if (e == cudaSuccess)
         e = wgrad<32, 16>(nx, ny, nz, c->B.dy, c->B.h2, c->B.part, 5, H, grad_dev + OFF_W3, grad_dev + OFF_B3, c->st);
-    if (e == cudaSuccess) e = conv<16, 32, EPI_MASK>(nx, ny, nz, c->B.dy, c->B.wd3, nullptr, c->B.h2, c->B.dz2, c->st);
+    if (e == cudaSuccess)
+        e = conv<16, 32, EPI_MASK>(nx, ny, nz, c->B.dy, c->B.wd3, nullptr, c->B.h2, c->B.dz2, c->B.tcerr, c->st);
     // layer 2
     if (e == cudaSuccess)
         e = wgrad<32, 32>(nx, ny, nz, c->B.dz2, c->B.h1, c->B.part, H, H, grad_dev + OFF_W2, grad_dev + OFF_B2, c->st);
-    if (e == cudaSuccess) e = conv<32, 32, EPI_MASK>(nx, ny, nz, c->B.dz2, c->B.wd2, nullptr, c->B.h1, c->B.dz1, c->st);
+    if (e == cudaSuccess)
+        e = conv<32, 32, EPI_MASK>(nx, ny, nz, c->B.dz2, c->B.wd2, nullptr, c->B.h1, c->B.dz1, c->B.tcerr, c->st);
     // layer 1
     if (e == cudaSuccess)
         e = wgrad<16, 32>(nx, ny, nz, c->B.dz1, c->B.x0, c->B.part, H, 5, grad_dev + OFF_W1, grad_dev + OFF_B1, c->st);
@@ -677,6 +872,22 @@ osb_status osb_closure_adam_step(osb_closure *c, const float *grad_dev, float lr
         return OSB_ERR_CUDA;
     }
     return osb_closure_sync_weights(c);
+}
+
+osb_status osb_closure_status(osb_closure *c) {
+    if (!c) return OSB_ERR_INVALID_ARG;
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, c->B.tcerr, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        set_last_error("closure: status read failed");
+        return OSB_ERR_CUDA;
+    }
+    if (h) {
+        set_last_error("closure: a tensor-core accumulator wait ran out");
+        return OSB_ERR_TIMEOUT;
+    }
+    return OSB_OK;
 }
 
 osb_status osb_box_filter(const double *fine_dev, int fnx, int fny, int fnz, int factor, double *coarse_dev,

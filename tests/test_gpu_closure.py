@@ -126,3 +126,33 @@ def test_training_reduces_a_priori_error(mods):
     assert base == pytest.approx(1.0)
     assert hist[-1] < 0.5 * hist[0]
     assert after < 0.8, (after, hist[:3], hist[-3:])
+
+
+def test_tensor_core_convolutions_match_oracle(mods):
+    """Grids with ny a multiple of 16 take the tcgen05 path (TMEM accumulator)
+    for the 32-channel convolutions: forward and every gradient block vs the
+    CPU oracle, and no accumulator wait ran out."""
+    osb, closure, torch = mods
+    c, theta, Q, C, mean, std, out = _setup(mods, n=(16, 16, 8), seed=11)
+    Qd, Cd = torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda()
+    Cg = c.forward(Qd).cpu().numpy()
+    assert _rel(Cg, co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16")) < 1e-2
+    loss, grad = c.loss_grad(Qd, Cd)
+    lo, go = co.loss_grad(theta.astype(np.float64), Q, C, mean, std, out, mode="bf16")
+    assert float(loss.item()) == pytest.approx(lo, rel=1e-3)
+    P, Po = co.unpack(grad.cpu().numpy().astype(np.float64)), co.unpack(go)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert _rel(P[name], Po[name]) < 2e-2, name
+    c.status()
+
+
+def test_tensor_core_and_mma_sync_paths_agree(mods, monkeypatch):
+    osb, closure, torch = mods
+    c, theta, Q, C, *_ = _setup(mods, n=(32, 16, 4), seed=13)
+    Qd = torch.from_numpy(Q).cuda()
+    monkeypatch.setenv("OSB_CLOSURE_MMA", "sync")
+    ref = c.forward(Qd).cpu().numpy()
+    monkeypatch.setenv("OSB_CLOSURE_MMA", "tc")
+    tc = c.forward(Qd).cpu().numpy()
+    c.status()
+    assert _rel(tc, ref) < 5e-3
