@@ -50,6 +50,9 @@ struct osb_grid {
     std::map<std::string, cudaGraphExec_t> *graphs;
     cudaStream_t capture_st;  // library-owned stream the batch graphs are captured on
     osb_closure *closure;     // learned correction added to R in every stage, or nullptr
+    // FP32 z-march stage: TMA descriptors per stage source q[b] (b = 0, 1)
+    zm::ZTma *ztma;           // [2 sources][flux, rhs]
+    int *kerr;                // device error word of bounded in-kernel waits
 };
 
 namespace {
@@ -142,6 +145,75 @@ OrderKernels kernels_for(int order) {
     }
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        (void)cudaGetLastError();
+    }
+    return fn;
+}
+
+bool encode_plane_map(CUtensorMap *m, const float *base, const Dims &d, int bx, int by) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.nx * d.ny * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)base, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// TMA descriptors of the FP32 z-march kernels for both stage sources q[0],
+// q[1].  Left unused (cp.async loads) when the x extent is not a multiple of 4
+// (row strides must be 16-byte multiples), the order is above 8, or
+// OSB_FP32_LOADS=cpasync.
+void build_ztma(osb_grid *g) {
+    g->ztma = nullptr;
+    if (g->desc.precision != OSB_FP32 || g->desc.order > 8 || g->d.nx % 4) return;
+    const char *env = getenv("OSB_FP32_LOADS");
+    if (env && strcmp(env, "cpasync") == 0) return;
+    zm::ZTma *t = new (std::nothrow) zm::ZTma[4];
+    if (!t) return;
+    memset(t, 0, 4 * sizeof(zm::ZTma));
+    const int rh = 8 + 2 * (g->desc.order / 2);
+    const float *aux = (const float *)g->aux;
+    const size_t as = g->aux_stride;
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        const float *q = (const float *)g->q[b];
+        const size_t qs = g->q_stride;
+        zm::ZTma &fl = t[2 * b], &rh_ = t[2 * b + 1];
+        for (int f = 0; f < 4; ++f) ok = ok && encode_plane_map(&fl.rect[f], q + f * qs, g->d, 40, rh);
+        ok = ok && encode_plane_map(&fl.col[0], q + 4 * qs, g->d, 32, 8);
+        for (int f = 0; f < 5; ++f) ok = ok && encode_plane_map(&rh_.rect[f], q + f * qs, g->d, 40, rh);
+        const int af[4] = {A_FX, A_FY, A_GX, A_GY};
+        for (int f = 0; f < 4; ++f) ok = ok && encode_plane_map(&rh_.rect[5 + f], aux + af[f] * as, g->d, 40, rh);
+        ok = ok && encode_plane_map(&rh_.col[0], aux + A_FZ * as, g->d, 32, 8);
+        ok = ok && encode_plane_map(&rh_.col[1], aux + A_GZ * as, g->d, 32, 8);
+        fl.use = rh_.use = 1;
+    }
+    if (!ok) {
+        delete[] t;
+        return;
+    }
+    g->ztma = t;
+}
+
 StageArgs base_args(const osb_grid *g) {
     StageArgs a;
     memset(&a, 0, sizeof(a));
@@ -152,6 +224,7 @@ StageArgs base_args(const osb_grid *g) {
     a.precision = g->desc.precision;
     a.visc_form = g->desc.visc_form;
     a.zmarch = g->zmarch;
+    a.kerr = g->kerr;
     a.aux = g->aux;
     a.aux_stride = g->aux_stride;
     a.u_stride = g->u_stride;
@@ -262,6 +335,12 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     g->result = g->partials + (size_t)g->max_partials * DIAG_STRIDE;
     g->batch_rec = (BatchInst *)(g->ws + aux_bytes(desc) + diag_bytes(desc));
     g->batch_ctl = (char *)g->batch_rec + round256(sizeof(BatchInst));
+    g->kerr = (int *)(g->batch_ctl + BATCH_CTL_BYTES - sizeof(int));
+    if (cudaMemsetAsync(g->kerr, 0, sizeof(int), g->st) != cudaSuccess) {
+        delete g;
+        return cuda_fail(cudaErrorInvalidValue, "grid create: error word reset");
+    }
+    build_ztma(g);
     g->cur = 0;
     {
         const char *env = getenv("OSB_FP32_STAGE");
@@ -287,6 +366,7 @@ osb_status osb_grid_destroy(osb_grid *g) {
         delete g->graphs;
     }
     if (g->capture_st) cudaStreamDestroy(g->capture_st);
+    delete[] g->ztma;
     delete g;
     return OSB_OK;
 }
@@ -455,6 +535,11 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     a.alpha_dt = RK_ALPHA[k] * g->prm.dt;
     a.beta_dt = RK_BETA[k] * g->prm.dt;
     a.ev = nullptr;
+    if (f32 && g->ztma) {
+        const int b = (a.src == g->q[0]) ? 0 : 1;
+        a.ztma_flux = &g->ztma[2 * b];
+        a.ztma_rhs = &g->ztma[2 * b + 1];
+    }
     return a;
 }
 
@@ -504,8 +589,11 @@ osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
                                        g->partials, g->max_partials, g->result, g->st);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
     double h[NDIAG];
+    int herr = 0;
     e = cudaMemcpyAsync(h, g->result, sizeof(h), cudaMemcpyDeviceToHost, g->st);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics copy");
+    e = cudaMemcpyAsync(&herr, g->kerr, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "diagnostics status copy");
     e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics sync");
     out->t = g->t;
@@ -515,6 +603,7 @@ osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
     for (int m = 0; m < 5; ++m) out->total[m] = h[2 + m];
     out->nonfinite = (long long)h[7];
     out->max_cfl = h[8];
+    if (herr) return fail(OSB_ERR_TIMEOUT, "a bounded in-kernel wait of an earlier step ran out; the state is invalid");
     if (out->nonfinite > 0) return fail(OSB_ERR_NONFINITE, "state holds non-finite values");
     return OSB_OK;
 }

@@ -8,6 +8,7 @@
 //                  stage), then the diagnostics partial sums and result.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -85,7 +86,20 @@ struct StageArgs {
     cudaEvent_t *ev;        // optional: 4 events recorded around the 3 kernels
     int zmarch;             // FP32 path: 1 = z-marching two-kernel stage, 0 = three-kernel stage
     const float *closure;   // learned correction added to R (5 fields, stride d.n), or nullptr
+    const void *ztma_flux;  // host: TMA descriptors of the z-march kernels for this stage, or nullptr
+    const void *ztma_rhs;
+    int *kerr;              // device word set when a bounded in-kernel wait ran out
 };
+
+namespace zm {
+// TMA descriptors of one z-march stage: haloed plane boxes (40 x (8 + 2R) x 1)
+// of the ring fields and tile boxes (32 x 8 x 1) of the column-only fields.
+struct ZTma {
+    CUtensorMap rect[9];
+    CUtensorMap col[2];
+    int use;
+};
+}  // namespace zm
 
 // Kernel kinds reported by the profiling hooks.
 enum KernelKind { KK_PRIM = 0, KK_GRAD = 1, KK_RESID = 2, KK_COUNT = 3 };

@@ -2,11 +2,14 @@
 // work form A), the memory-lean form of the three kernels in stage.cuh.
 //
 // Each CTA owns a TX x TY column tile of the grid and a chunk of z planes.
-// Planes stream through a shared-memory ring: plane L is copied with
-// cp.async (4-byte copies at wrapped addresses, so the periodic halo needs no
-// ghost cells) PF planes ahead of its use, over the tile plus an R-wide halo
-// in x and y.  Along z every thread keeps its own column in register queues of
-// 2R+1 values; x/y stencils read the ring, z stencils read the queues.
+// Planes stream through a shared-memory ring PF planes ahead of their use,
+// over the tile plus a halo (R rows in y; 4 columns in x, so that every row
+// starts on a 16-byte boundary).  Tiles away from the periodic boundary load
+// each field's plane with one TMA box copy (cp.async.bulk.tensor.3d) that
+// completes on the slot's mbarrier; tiles touching the boundary use 4-byte
+// cp.async copies at wrapped addresses (TMA fills out-of-range boxes with zeros
+// instead of wrapping).  Along z every thread keeps its own column in register
+// queues of 2R+1 values; x/y stencils read the ring, z stencils the queues.
 //
 //   k_zflux: velocity gradient -> energy flux F_j (with the viscous work
 //            u_i tau_ij), g_i = div u - D_i u_i, div u          (7 FP32 fields)
@@ -17,19 +20,55 @@
 // (20 B) and U (40 B), plus the 20 B FP32 copy of U in the last stage.
 #pragma once
 
+#include <cuda.h>
+#include <stddef.h>
+
 #include "stage.cuh"
 
 namespace osb {
 namespace zm {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int PF = 2;  // planes in flight ahead of the lead plane
+constexpr int PF = 1;   // planes in flight ahead of the lead plane
+constexpr int CX = 4;   // ring column of the tile's first x (row start x0 - 4 is 16-byte aligned)
+constexpr unsigned ZM_WAIT_LIMIT = 1u << 24;
 
 template <int R>
 struct Geo {
-    static constexpr int RW = TX + 2 * R, RH = TY + 2 * R, RA = RW * RH;
-    static constexpr int NS = R + 1 + PF;  // ring slots
+    static constexpr int RW = TX + 2 * CX, RH = TY + 2 * R, RA = RW * RH;
+    static constexpr int RAP = (RA + 31) / 32 * 32;  // ring plane stride: TMA destinations need 128-byte alignment
+    static constexpr int NS = R + 1 + PF;            // ring slots
 };
+
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_load3(void *dst, const CUtensorMap *map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void bar_init(uint32_t bar, int count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void bar_expect(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Bounded wait for the given phase parity; false if the limit ran out.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (unsigned it = 0; it < ZM_WAIT_LIMIT; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(32);
+    }
+    return false;
+}
 
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -52,7 +91,7 @@ __device__ __forceinline__ void make_offsets(int *off, int x0, int y0, const Dim
     using G = Geo<R>;
     for (int e = threadIdx.x; e < G::RA; e += NT) {
         const int ry = e / G::RW, rx = e - ry * G::RW;
-        off[e] = wrapc(y0 + ry - R, d.ny) * d.nx + wrapc(x0 + rx - R, d.nx);
+        off[e] = wrapc(y0 + ry - R, d.ny) * d.nx + wrapc(x0 + rx - CX, d.nx);
     }
 }
 
@@ -116,43 +155,71 @@ __device__ __forceinline__ float sdy2(const float *p, int ce, const float *c) {
 template <int R>
 struct FluxSmem {
     using G = Geo<R>;
-    int off[G::RA];
-    float ring[G::NS][4][G::RA];  // rho, m0, m1, m2 over the rectangle
+    float ring[G::NS][4][G::RAP];  // rho, m0, m1, m2 over the rectangle (TMA destinations first)
     float ering[G::NS][NT];       // rho E at the tile points
     float vel[3][G::RA];          // u_i of the output plane
+    int off[G::RA];
+    unsigned long long bars[G::NS];
 };
 
 template <int R>
-__global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk) {
+__global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, const __grid_constant__ ZTma tm) {
     using G = Geo<R>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     FluxSmem<R> &S = *reinterpret_cast<FluxSmem<R> *>(smem_raw);
     const Dims d = a.d;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, d.nz);
-    const int ce = (ty + R) * G::RW + tx + R;
+    const int ce = (ty + R) * G::RW + tx + CX;
     const bool active = (x0 + tx < d.nx) && (y0 + ty < d.ny);
     const int plane = d.nx * d.ny;
     const float *Q = static_cast<const float *>(a.src);
     const size_t qs = a.src_stride, as = a.aux_stride;
     float *aux = static_cast<float *>(a.aux);
     const Coef<float> &c = a.c32;
+    const bool use_tma = tm.use && x0 >= CX && x0 - CX + G::RW <= d.nx && y0 >= R && y0 + TY + R <= d.ny;
 
     make_offsets<R>(S.off, x0, y0, d);
+    if (tid == 0) {
+        for (int s = 0; s < G::NS; ++s) bar_init(smem_u32(&S.bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     const int coff = S.off[ce];
+    uint32_t phase = 0;
 
     auto issue = [&](int L) {
         const int s = ((L % G::NS) + G::NS) % G::NS;
-        const size_t zb = (size_t)wrapz(L, d.nz) * plane;
-        for (int e = tid; e < G::RA; e += NT) {
-            const size_t g = zb + S.off[e];
+        const int zc = wrapz(L, d.nz);
+        if (use_tma) {
+            if (tid == 0) {
+                const uint32_t bar = smem_u32(&S.bars[s]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_expect(bar, (uint32_t)((4 * G::RA + NT) * sizeof(float)));
 #pragma unroll
-            for (int f = 0; f < 4; ++f) cp_async4(&S.ring[s][f][e], Q + f * qs + g);
+                for (int f = 0; f < 4; ++f) tma_load3(&S.ring[s][f][0], &tm.rect[f], x0 - CX, y0 - R, zc, bar);
+                tma_load3(&S.ering[s][0], &tm.col[0], x0, y0, zc, bar);
+            }
+        } else {
+            const size_t zb = (size_t)zc * plane;
+            for (int e = tid; e < G::RA; e += NT) {
+                const size_t g = zb + S.off[e];
+#pragma unroll
+                for (int f = 0; f < 4; ++f) cp_async4(&S.ring[s][f][e], Q + f * qs + g);
+            }
+            cp_async4(&S.ering[s][tid], Q + 4 * qs + zb + coff);
+            cp_commit();
         }
-        cp_async4(&S.ering[s][tid], Q + 4 * qs + zb + coff);
-        cp_commit();
+    };
+    auto wait_plane = [&](int L) {
+        if (use_tma) {
+            const int s = ((L % G::NS) + G::NS) % G::NS;
+            if (!bar_wait(smem_u32(&S.bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
+            phase ^= 1u << s;
+        } else {
+            cp_wait<PF - 1>();
+        }
     };
 
     float qu[2 * R + 1], qv[2 * R + 1], qw[2 * R + 1];
@@ -165,11 +232,11 @@ __global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk) 
     const float ir = float(a.ph.inv_re), gm1 = float(a.ph.gm1);
 #pragma unroll 1
     for (int L = Lbeg; L < Lend; ++L) {
-        cp_wait<PF - 1>();
+        wait_plane(L);
         __syncthreads();
         if (L + PF < Lend)
             issue(L + PF);
-        else
+        else if (!use_tma)
             cp_commit();  // keep the group count uniform
         const int sL = ((L % G::NS) + G::NS) % G::NS;
         {
@@ -226,47 +293,77 @@ enum DerField { DF_U = 0, DF_V, DF_W, DF_T, DF_PXX, DF_PYY, DF_PXY, DF_PXZ, DF_P
 template <int R>
 struct RhsSmem {
     using G = Geo<R>;
-    int off[G::RA];
-    float ring[G::NS][RF_N][G::RA];
-    float cring[G::NS][2][NT];  // F_z, g_z at the tile points
+    float ring[G::NS][RF_N][G::RAP];  // TMA destinations first
+    float cring[G::NS][2][NT];       // F_z, g_z at the tile points
     float der[DF_N][G::RA];
+    int off[G::RA];
+    unsigned long long bars[G::NS];
 };
 
 template <int R>
-__global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a, int zchunk) {
+__global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a, int zchunk,
+                                                                const __grid_constant__ ZTma tm) {
     using G = Geo<R>;
     constexpr int Q = 2 * R + 1;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     RhsSmem<R> &S = *reinterpret_cast<RhsSmem<R> *>(smem_raw);
     const Dims d = a.d;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, d.nz);
-    const int ce = (ty + R) * G::RW + tx + R;
+    const int ce = (ty + R) * G::RW + tx + CX;
     const bool active = (x0 + tx < d.nx) && (y0 + ty < d.ny);
     const int plane = d.nx * d.ny;
     const float *Qg = static_cast<const float *>(a.src);
     const size_t qs = a.src_stride, as = a.aux_stride;
     const float *aux = static_cast<const float *>(a.aux);
     const Coef<float> &c = a.c32;
+    const bool use_tma = tm.use && x0 >= CX && x0 - CX + G::RW <= d.nx && y0 >= R && y0 + TY + R <= d.ny;
 
     make_offsets<R>(S.off, x0, y0, d);
+    if (tid == 0) {
+        for (int s = 0; s < G::NS; ++s) bar_init(smem_u32(&S.bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
     const int coff = S.off[ce];
+    uint32_t phase = 0;
 
     auto issue = [&](int L) {
         const int s = ((L % G::NS) + G::NS) % G::NS;
-        const size_t zb = (size_t)wrapz(L, d.nz) * plane;
-        const float *src[RF_N] = {Qg, Qg + qs, Qg + 2 * qs, Qg + 3 * qs, Qg + 4 * qs,
-                                  aux + A_FX * as, aux + A_FY * as, aux + A_GX * as, aux + A_GY * as};
-        for (int e = tid; e < G::RA; e += NT) {
-            const size_t g = zb + S.off[e];
+        const int zc = wrapz(L, d.nz);
+        if (use_tma) {
+            if (tid == 0) {
+                const uint32_t bar = smem_u32(&S.bars[s]);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bar_expect(bar, (uint32_t)((RF_N * G::RA + 2 * NT) * sizeof(float)));
 #pragma unroll
-            for (int f = 0; f < RF_N; ++f) cp_async4(&S.ring[s][f][e], src[f] + g);
+                for (int f = 0; f < RF_N; ++f) tma_load3(&S.ring[s][f][0], &tm.rect[f], x0 - CX, y0 - R, zc, bar);
+                tma_load3(&S.cring[s][0][0], &tm.col[0], x0, y0, zc, bar);
+                tma_load3(&S.cring[s][1][0], &tm.col[1], x0, y0, zc, bar);
+            }
+        } else {
+            const size_t zb = (size_t)zc * plane;
+            const float *src[RF_N] = {Qg, Qg + qs, Qg + 2 * qs, Qg + 3 * qs, Qg + 4 * qs,
+                                      aux + A_FX * as, aux + A_FY * as, aux + A_GX * as, aux + A_GY * as};
+            for (int e = tid; e < G::RA; e += NT) {
+                const size_t g = zb + S.off[e];
+#pragma unroll
+                for (int f = 0; f < RF_N; ++f) cp_async4(&S.ring[s][f][e], src[f] + g);
+            }
+            cp_async4(&S.cring[s][0][tid], aux + A_FZ * as + zb + coff);
+            cp_async4(&S.cring[s][1][tid], aux + A_GZ * as + zb + coff);
+            cp_commit();
         }
-        cp_async4(&S.cring[s][0][tid], aux + A_FZ * as + zb + coff);
-        cp_async4(&S.cring[s][1][tid], aux + A_GZ * as + zb + coff);
-        cp_commit();
+    };
+    auto wait_plane = [&](int L) {
+        if (use_tma) {
+            const int s = ((L % G::NS) + G::NS) % G::NS;
+            if (!bar_wait(smem_u32(&S.bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
+            phase ^= 1u << s;
+        } else {
+            cp_wait<PF - 1>();
+        }
     };
 
     // register queues along z (planes zo-R .. zo+R once full)
@@ -288,11 +385,11 @@ __global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a
     for (int p = 0; p < PF; ++p) issue(Lbeg + p);
 #pragma unroll 1
     for (int L = Lbeg; L < Lend; ++L) {
-        cp_wait<PF - 1>();
+        wait_plane(L);
         __syncthreads();
         if (L + PF < Lend)
             issue(L + PF);
-        else
+        else if (!use_tma)
             cp_commit();
         const int sL = ((L % G::NS) + G::NS) % G::NS;
         {   // lead plane: point-wise quantities of this thread's column
@@ -385,10 +482,14 @@ __global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a
 
 template <int R>
 constexpr size_t flux_smem() {
+    static_assert(Geo<R>::RAP * sizeof(float) % 128 == 0 && offsetof(FluxSmem<R>, ering) % 128 == 0,
+                  "TMA destinations must be 128-byte aligned");
     return sizeof(FluxSmem<R>);
 }
 template <int R>
 constexpr size_t rhs_smem() {
+    static_assert(Geo<R>::RAP * sizeof(float) % 128 == 0 && offsetof(RhsSmem<R>, cring) % 128 == 0,
+                  "TMA destinations must be 128-byte aligned");
     return sizeof(RhsSmem<R>);
 }
 
@@ -403,11 +504,14 @@ cudaError_t launch_zstage(const StageArgs &a) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_zrhs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
     if (e != cudaSuccess) return e;
+    static const ZTma none = {};
+    const ZTma &tf = a.ztma_flux ? *static_cast<const ZTma *>(a.ztma_flux) : none;
+    const ZTma &tr = a.ztma_rhs ? *static_cast<const ZTma *>(a.ztma_rhs) : none;
     if (a.ev) cudaEventRecord(a.ev[0], a.stream);
     if (a.ev) cudaEventRecord(a.ev[1], a.stream);  // no separate primitive kernel
-    k_zflux<R><<<grd, NT, sf, a.stream>>>(a, zchunk);
+    k_zflux<R><<<grd, NT, sf, a.stream>>>(a, zchunk, tf);
     if (a.ev) cudaEventRecord(a.ev[2], a.stream);
-    k_zrhs<R><<<grd, NT, sr, a.stream>>>(a, zchunk);
+    k_zrhs<R><<<grd, NT, sr, a.stream>>>(a, zchunk, tr);
     if (a.ev) cudaEventRecord(a.ev[3], a.stream);
     return cudaGetLastError();
 }
