@@ -139,7 +139,10 @@ osb_status osb_residual(osb_grid *grid, double *R_dev);
  * Runge-Kutta scheme (Section 2.4): for k = 1..3,
  *   q_k = U_{k-1} + alpha_k dt R(q_{k-1}),  U_k = U_{k-1} + beta_k dt R(q_{k-1}),
  * alpha = (2/3, 5/12, 3/5), beta = (1/4, 3/20, 3/5), q_0 = U_0 = Q^n,
- * Q^{n+1} = U_3.  Stream-ordered, no sync.  nsteps >= 0. */
+ * Q^{n+1} = U_3.  Stream-ordered, no sync.  nsteps >= 0.  Runs of two or more
+ * steps (no closure attached, no profiling) replay a CUDA graph of one step,
+ * captured on first use on a library-owned stream (set OSB_GRAPHS=0 to
+ * launch the kernels directly); results are identical either way. */
 osb_status osb_rk3_step(osb_grid *grid, int nsteps);
 
 /* Computes the diagnostics of the current state into *out (FP64 reductions,

@@ -53,6 +53,7 @@ struct osb_grid {
     // FP32 z-march stage: TMA descriptors per stage source q[b] (b = 0, 1)
     zm::ZTma *ztma;           // [2 sources][flux, rhs]
     int *kerr;                // device error word of bounded in-kernel waits
+    cudaGraphExec_t step_graph[2];  // one RK3 step starting with Q^n in U[0] / U[1]
 };
 
 namespace {
@@ -366,6 +367,8 @@ osb_status osb_grid_destroy(osb_grid *g) {
         delete g->graphs;
     }
     if (g->capture_st) cudaStreamDestroy(g->capture_st);
+    for (int b = 0; b < 2; ++b)
+        if (g->step_graph[b]) cudaGraphExecDestroy(g->step_graph[b]);
     delete[] g->ztma;
     delete g;
     return OSB_OK;
@@ -574,8 +577,66 @@ static osb_status rk3_one_step(osb_grid *g) {
     return OSB_OK;
 }
 
+// The launches of one RK3 step (3 stages) captured into a CUDA graph on a
+// library-owned stream; replayed on the grid's stream.  Used for runs of two
+// or more steps without a closure or profiling: a step is 6-9 kernel launches,
+// which dominate on small grids.
+static osb_status step_graph(osb_grid *g, int cur, cudaGraphExec_t *out) {
+    if (g->step_graph[cur]) {
+        *out = g->step_graph[cur];
+        return OSB_OK;
+    }
+    if (!g->capture_st) {
+        cudaError_t ec = cudaStreamCreateWithFlags(&g->capture_st, cudaStreamNonBlocking);
+        if (ec != cudaSuccess) {
+            g->capture_st = nullptr;
+            return cuda_fail(ec, "step capture stream");
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(g->capture_st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "step capture begin");
+    cudaError_t el = cudaSuccess;
+    for (int k = 0; k < 3 && el == cudaSuccess; ++k) {
+        StageArgs a = stage_args(g, cur, k);
+        a.stream = g->capture_st;
+        el = g->K.stage(a);
+    }
+    e = cudaStreamEndCapture(g->capture_st, &graph);
+    if (el != cudaSuccess || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(el != cudaSuccess ? el : e, "step capture");
+    }
+    e = cudaGraphInstantiate(&g->step_graph[cur], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g->step_graph[cur] = nullptr;
+        return cuda_fail(e, "step graph instantiate");
+    }
+    *out = g->step_graph[cur];
+    return OSB_OK;
+}
+
 osb_status osb_rk3_step(osb_grid *g, int nsteps) {
     if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    const char *env = getenv("OSB_GRAPHS");
+    const bool graphs = nsteps >= 2 && !g->closure && !g->prof_ev && !(env && strcmp(env, "0") == 0);
+    if (graphs) {
+        osb_status s0 = ensure_f32_copy(g);
+        if (s0 != OSB_OK) return s0;
+        for (int s = 0; s < nsteps; ++s) {
+            cudaGraphExec_t ge = nullptr;
+            osb_status st = step_graph(g, g->cur, &ge);
+            if (st != OSB_OK) return st;
+            cudaError_t e = cudaGraphLaunch(ge, g->st);
+            if (e != cudaSuccess) return cuda_fail(e, "step graph launch");
+            g->cur = 1 - g->cur;
+            g->qc = g->cur;
+            g->step += 1;
+            g->t = g->step * g->prm.dt;
+        }
+        return OSB_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
         osb_status st = rk3_one_step(g);
         if (st != OSB_OK) return st;

@@ -497,7 +497,11 @@ constexpr size_t rhs_smem() {
 template <int R>
 cudaError_t launch_zstage(const StageArgs &a) {
     static_assert(R <= 4, "z-march kernels are built for orders up to 8");
-    const int zchunk = 32;
+    // z planes per CTA: long chunks amortise the 2R-plane warm-up of the z
+    // queues; short chunks give small grids enough CTAs (about four per SM)
+    const int tiles_xy = ((a.d.nx + TX - 1) / TX) * ((a.d.ny + TY - 1) / TY);
+    int zchunk = (int)(((long long)a.d.nz * tiles_xy + 4 * 152 - 1) / (4 * 152));
+    zchunk = zchunk < 4 ? 4 : (zchunk > 32 ? 32 : zchunk);
     dim3 grd((a.d.nx + TX - 1) / TX, (a.d.ny + TY - 1) / TY, (a.d.nz + zchunk - 1) / zchunk);
     const size_t sf = flux_smem<R>(), sr = rhs_smem<R>();
     cudaError_t e = cudaFuncSetAttribute(k_zflux<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);

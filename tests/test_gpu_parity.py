@@ -343,3 +343,20 @@ def test_fp32_tma_and_cpasync_loads_are_bitwise_equal(osb, dims, order, monkeypa
     Qo = orc.rk3_step(case, orc.tgv_init(case, noise, 1e-2), 4)
     for m, err in enumerate(_fp32_err(out[0], Qo)):
         assert err < 1e-5, (m, err)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replayed_steps_equal_direct_launches(osb, precision, monkeypatch):
+    """Multi-step calls replay a captured CUDA graph of one step; the state is
+    bitwise the one of direct launches (one call per step)."""
+    n = 24
+    noise = inputs.gaussian_noise(n, n, n, seed=41)
+    a = _grid(osb, n, n, n, order=4, precision=precision)
+    b = _grid(osb, n, n, n, order=4, precision=precision)
+    a.init_taylor_green(noise, 1e-3)
+    b.init_taylor_green(noise, 1e-3)
+    a.step(7)
+    for _ in range(7):
+        b.step(1)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert a.diagnostics()["step"] == 7
