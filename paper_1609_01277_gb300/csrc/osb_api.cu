@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <new>
@@ -723,7 +724,8 @@ int tile_depth(const osb_grid_desc &d) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load_locked();
     auto it = g_tune->find(shape_key(d));
-    return it == g_tune->end() ? 4 : it->second;
+    if (it != g_tune->end()) return it->second;
+    return d.precision == OSB_FP32 ? 8 : 4;
 }
 
 osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
@@ -744,9 +746,14 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     }
     if (nsteps == 0) return OSB_OK;
     cudaStream_t st = g0->st;
+    // FP32 form-A ensembles of orders <= 8 run z-march work items (row starts
+    // must be 16-byte aligned: x extents multiples of 4)
+    bool zmode = g0->desc.precision == OSB_FP32 && g0->desc.visc_form == OSB_VISC_A && g0->desc.order <= 8;
+    for (int i = 0; i < n && zmode; ++i) zmode = grids[i]->zmarch && grids[i]->d.nx % 4 == 0;
     BatchParams P;
     memset(&P, 0, sizeof(P));
     P.n = n;
+    P.phases = zmode ? 6 : 9;
     P.prefix[0] = 0;
     std::string key = std::to_string(nsteps) + "|" + std::to_string(g_batch_cfg.test_stall) + "|" +
                       std::to_string((long long)(g_batch_cfg.wait_limit_s * 1e9));
@@ -754,14 +761,24 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
         osb_grid *g = grids[i];
         osb_status s0 = ensure_f32_copy(g);
         if (s0 != OSB_OK) return s0;
-        BatchInst rec;
+        static BatchInst rec;  // host staging of one record (large: holds TMA descriptors)
         memset(&rec, 0, sizeof(rec));
         for (int par = 0; par < 2; ++par)
-            for (int k = 0; k < 3; ++k) rec.st[par][k] = stage_args(g, par, k);
+            for (int k = 0; k < 3; ++k) {
+                rec.st[par][k] = stage_args(g, par, k);
+                rec.st[par][k].ztma_flux = rec.st[par][k].ztma_rhs = nullptr;  // host pointers: not used on the device
+                rec.zsrc[par][k] = (rec.st[par][k].src == g->q[0]) ? 0 : 1;
+            }
         rec.tz = tile_depth(g->desc);
         rec.tiles_x = (g->d.nx + BX - 1) / BX;
         rec.tiles_y = (g->d.ny + BY - 1) / BY;
         rec.tiles_z = (g->d.nz + rec.tz - 1) / rec.tz;
+        if (zmode && g->ztma)
+            for (int b = 0; b < 2; ++b) {
+                rec.tma[b][0] = g->ztma[2 * b];
+                rec.tma[b][1] = g->ztma[2 * b + 1];
+            }
+        // pageable source: staged before the call returns, so rec can be reused
         cudaError_t e = cudaMemcpyAsync(g->batch_rec, &rec, sizeof(rec), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "batch record upload");
         const long long tiles = (long long)rec.tiles_x * rec.tiles_y * rec.tiles_z;
@@ -770,12 +787,14 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
         P.rec[i] = g->batch_rec;
         P.p0[i] = g->cur;
         char b[64];
-        snprintf(b, sizeof b, "|%p:%d:%d", (void *)g, g->cur, rec.tz);
+        snprintf(b, sizeof b, "|%p:%d:%d:%d", (void *)g, g->cur, rec.tz, (int)zmode);
         key += b;
     }
     P.tiles_total = P.prefix[n];
-    P.total_items = (long long)nsteps * 9 * P.tiles_total;
-    if ((long long)nsteps * 9 * (P.prefix[n] - P.prefix[n - 1]) > 0xffffffffLL)
+    P.total_items = (long long)nsteps * P.phases * P.tiles_total;
+    long long max_tiles = 0;
+    for (int i = 0; i < n; ++i) max_tiles = std::max(max_tiles, (long long)(P.prefix[i + 1] - P.prefix[i]));
+    if ((long long)nsteps * P.phases * max_tiles > 0xffffffffLL)
         return fail(OSB_ERR_INVALID_ARG, "batch: too many steps for the 32-bit completion counters");
     P.timeout_ns = (long long)(g_batch_cfg.wait_limit_s * 1e9);
     P.inject_stall = g_batch_cfg.test_stall;
@@ -808,7 +827,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
         cudaError_t e1 = cudaMemsetAsync(ctl, 0, 16 + sizeof(unsigned) * MAXB, cs);
-        cudaError_t e2 = launch_batch(P, g0->desc.order, g0->desc.precision, g0->desc.visc_form, cs);
+        cudaError_t e2 = launch_batch(P, g0->desc.order, g0->desc.precision, g0->desc.visc_form, (int)zmode, cs);
         e = cudaStreamEndCapture(cs, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -877,14 +896,16 @@ osb_status osb_autotune(osb_grid *g, int trial_steps, int *best_tz) {
     osb_status s = osb_get_state(g, saved.data());
     if (s != OSB_OK) return s;
     const std::string key = shape_key(g->desc);
-    const int cand[] = {1, 2, 4, 8, 16};
+    const int cand64[] = {1, 2, 4, 8, 16}, cand32[] = {4, 8, 16, 32, 0};
+    const int *cand = g->desc.precision == OSB_FP32 ? cand32 : cand64;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return fail(OSB_ERR_CUDA, "autotune: event create failed");
     int best = 4;
     float best_ms = 1e30f;
-    for (int tz : cand) {
-        if (tz > g->d.nz && tz != 1) continue;
+    for (int ci = 0; ci < 5; ++ci) {
+        const int tz = cand[ci];
+        if (tz == 0 || (tz > g->d.nz && tz != cand[0])) continue;
         {
             std::lock_guard<std::mutex> lock(g_tune_mu);
             tune_load_locked();

@@ -91,15 +91,6 @@ struct StageArgs {
     int *kerr;              // device word set when a bounded in-kernel wait ran out
 };
 
-namespace zm {
-// TMA descriptors of one z-march stage: haloed plane boxes (40 x (8 + 2R) x 1)
-// of the ring fields and tile boxes (32 x 8 x 1) of the column-only fields.
-struct ZTma {
-    CUtensorMap rect[9];
-    CUtensorMap col[2];
-    int use;
-};
-}  // namespace zm
 
 // Kernel kinds reported by the profiling hooks.
 enum KernelKind { KK_PRIM = 0, KK_GRAD = 1, KK_RESID = 2, KK_COUNT = 3 };
@@ -118,18 +109,31 @@ OrderKernels kernels_o8();
 OrderKernels kernels_o10();
 OrderKernels kernels_o12();
 
+namespace zm {
+// TMA descriptors of one z-march stage: haloed plane boxes (40 x (8 + 2R) x 1)
+// of the ring fields and tile boxes (32 x 8 x 1) of the column-only fields.
+struct ZTma {
+    CUtensorMap rect[9];
+    CUtensorMap col[2];
+    int use;
+};
+}  // namespace zm
+
 // Persistent ensemble kernel (batch.cu).
 constexpr int MAXB = 128;  // instances per batch
 
 struct BatchInst {
-    StageArgs st[2][3];  // [parity of (cur)][RK stage]
-    int tz;              // z planes per tile
+    StageArgs st[2][3];   // [parity of (cur)][RK stage]
+    int tz;               // z planes per tile
     int tiles_x, tiles_y, tiles_z;
+    int zsrc[2][3];       // FP32 z-march items: stage register holding the stencil source
+    zm::ZTma tma[2][2];   // FP32 z-march items: [stage register][flux, rhs]
 };
 
 struct BatchParams {
     int n;
     int tiles_total;       // items per phase sequence, all instances
+    int phases;            // phases per step: 9 (three-kernel items) or 6 (FP32 z-march items)
     long long total_items;
     long long timeout_ns;  // bound on every dependency wait
     int inject_stall;      // test control: make the first wait unreachable
@@ -141,7 +145,7 @@ struct BatchParams {
     int *err;
 };
 
-cudaError_t launch_batch(const BatchParams &P, int order, int precision, int visc_form, cudaStream_t st);
+cudaError_t launch_batch(const BatchParams &P, int order, int precision, int visc_form, int zmode, cudaStream_t st);
 
 // Learned closure (closure.cu).
 namespace cl {

@@ -74,6 +74,10 @@ __device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -162,15 +166,17 @@ struct FluxSmem {
     unsigned long long bars[G::NS];
 };
 
-template <int R>
-__global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, const __grid_constant__ ZTma tm) {
+// One column tile (x0, y0) over planes [z0, z1) of k_zflux.  PERSIST: called
+// from the persistent ensemble kernel -- data written earlier in the same
+// launch is read through L2 only (TMA, 16-byte cp.async.cg, ld.global.cg).
+// bars: the NS ring-slot mbarriers (initialised by the caller); phase: their
+// parity bits, carried across calls.
+template <int R, bool PERSIST>
+__device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, int x0, int y0, int z0, int z1,
+                                           FluxSmem<R> &S, unsigned long long *bars, uint32_t &phase) {
     using G = Geo<R>;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    FluxSmem<R> &S = *reinterpret_cast<FluxSmem<R> *>(smem_raw);
     const Dims d = a.d;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, d.nz);
     const int ce = (ty + R) * G::RW + tx + CX;
     const bool active = (x0 + tx < d.nx) && (y0 + ty < d.ny);
     const int plane = d.nx * d.ny;
@@ -179,22 +185,18 @@ __global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, 
     float *aux = static_cast<float *>(a.aux);
     const Coef<float> &c = a.c32;
     const bool use_tma = tm.use && x0 >= CX && x0 - CX + G::RW <= d.nx && y0 >= R && y0 + TY + R <= d.ny;
+    const bool vec16 = (d.nx % 4) == 0;  // 16-byte chunks of a row never straddle the wrap
 
     make_offsets<R>(S.off, x0, y0, d);
-    if (tid == 0) {
-        for (int s = 0; s < G::NS; ++s) bar_init(smem_u32(&S.bars[s]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     __syncthreads();
     const int coff = S.off[ce];
-    uint32_t phase = 0;
 
     auto issue = [&](int L) {
         const int s = ((L % G::NS) + G::NS) % G::NS;
         const int zc = wrapz(L, d.nz);
         if (use_tma) {
             if (tid == 0) {
-                const uint32_t bar = smem_u32(&S.bars[s]);
+                const uint32_t bar = smem_u32(&bars[s]);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 bar_expect(bar, (uint32_t)((4 * G::RA + NT) * sizeof(float)));
 #pragma unroll
@@ -203,19 +205,33 @@ __global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, 
             }
         } else {
             const size_t zb = (size_t)zc * plane;
-            for (int e = tid; e < G::RA; e += NT) {
-                const size_t g = zb + S.off[e];
+            if (PERSIST || vec16) {
+                for (int ch = tid; ch < G::RA / 4; ch += NT) {
+                    const int e = ch * 4;
+                    const size_t g = zb + S.off[e];
 #pragma unroll
-                for (int f = 0; f < 4; ++f) cp_async4(&S.ring[s][f][e], Q + f * qs + g);
+                    for (int f = 0; f < 4; ++f) cp_async16_cg(&S.ring[s][f][e], Q + f * qs + g);
+                }
+                if (tid < NT / 4) {
+                    const int row = tid / (TX / 4), j = tid % (TX / 4);
+                    cp_async16_cg(&S.ering[s][row * TX + 4 * j],
+                                  Q + 4 * qs + zb + S.off[(row + R) * G::RW + CX + 4 * j]);
+                }
+            } else {
+                for (int e = tid; e < G::RA; e += NT) {
+                    const size_t g = zb + S.off[e];
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) cp_async4(&S.ring[s][f][e], Q + f * qs + g);
+                }
+                cp_async4(&S.ering[s][tid], Q + 4 * qs + zb + coff);
             }
-            cp_async4(&S.ering[s][tid], Q + 4 * qs + zb + coff);
             cp_commit();
         }
     };
     auto wait_plane = [&](int L) {
         if (use_tma) {
             const int s = ((L % G::NS) + G::NS) % G::NS;
-            if (!bar_wait(smem_u32(&S.bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
+            if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
             phase ^= 1u << s;
         } else {
             cp_wait<PF - 1>();
@@ -282,6 +298,21 @@ __global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, 
         }
     }
     cp_wait<0>();
+    __syncthreads();  // the ring may be refilled by the caller's next tile
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, const __grid_constant__ ZTma tm) {
+    using G = Geo<R>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FluxSmem<R> &S = *reinterpret_cast<FluxSmem<R> *>(smem_raw);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G::NS; ++s) bar_init(smem_u32(&S.bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t phase = 0;
+    const int z0 = blockIdx.z * zchunk;
+    zflux_body<R, false>(a, tm, blockIdx.x * TX, blockIdx.y * TY, z0, min(z0 + zchunk, a.d.nz), S, S.bars, phase);
 }
 
 // ---------------------------------------------------------------------------
@@ -300,17 +331,14 @@ struct RhsSmem {
     unsigned long long bars[G::NS];
 };
 
-template <int R>
-__global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a, int zchunk,
-                                                                const __grid_constant__ ZTma tm) {
+// One column tile of k_zrhs (see zflux_body for PERSIST, bars and phase).
+template <int R, bool PERSIST>
+__device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, int x0, int y0, int z0, int z1,
+                                          RhsSmem<R> &S, unsigned long long *bars, uint32_t &phase) {
     using G = Geo<R>;
     constexpr int Q = 2 * R + 1;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    RhsSmem<R> &S = *reinterpret_cast<RhsSmem<R> *>(smem_raw);
     const Dims d = a.d;
     const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zchunk, z1 = min(z0 + zchunk, d.nz);
     const int ce = (ty + R) * G::RW + tx + CX;
     const bool active = (x0 + tx < d.nx) && (y0 + ty < d.ny);
     const int plane = d.nx * d.ny;
@@ -319,22 +347,18 @@ __global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a
     const float *aux = static_cast<const float *>(a.aux);
     const Coef<float> &c = a.c32;
     const bool use_tma = tm.use && x0 >= CX && x0 - CX + G::RW <= d.nx && y0 >= R && y0 + TY + R <= d.ny;
+    const bool vec16 = (d.nx % 4) == 0;
 
     make_offsets<R>(S.off, x0, y0, d);
-    if (tid == 0) {
-        for (int s = 0; s < G::NS; ++s) bar_init(smem_u32(&S.bars[s]), 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
     __syncthreads();
     const int coff = S.off[ce];
-    uint32_t phase = 0;
 
     auto issue = [&](int L) {
         const int s = ((L % G::NS) + G::NS) % G::NS;
         const int zc = wrapz(L, d.nz);
         if (use_tma) {
             if (tid == 0) {
-                const uint32_t bar = smem_u32(&S.bars[s]);
+                const uint32_t bar = smem_u32(&bars[s]);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 bar_expect(bar, (uint32_t)((RF_N * G::RA + 2 * NT) * sizeof(float)));
 #pragma unroll
@@ -346,20 +370,35 @@ __global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a
             const size_t zb = (size_t)zc * plane;
             const float *src[RF_N] = {Qg, Qg + qs, Qg + 2 * qs, Qg + 3 * qs, Qg + 4 * qs,
                                       aux + A_FX * as, aux + A_FY * as, aux + A_GX * as, aux + A_GY * as};
-            for (int e = tid; e < G::RA; e += NT) {
-                const size_t g = zb + S.off[e];
+            if (PERSIST || vec16) {
+                for (int ch = tid; ch < G::RA / 4; ch += NT) {
+                    const int e = ch * 4;
+                    const size_t g = zb + S.off[e];
 #pragma unroll
-                for (int f = 0; f < RF_N; ++f) cp_async4(&S.ring[s][f][e], src[f] + g);
+                    for (int f = 0; f < RF_N; ++f) cp_async16_cg(&S.ring[s][f][e], src[f] + g);
+                }
+                if (tid < NT / 2) {
+                    const int cf = tid / (NT / 4), t4 = tid % (NT / 4);
+                    const int row = t4 / (TX / 4), j = t4 % (TX / 4);
+                    cp_async16_cg(&S.cring[s][cf][row * TX + 4 * j],
+                                  aux + (cf ? A_GZ : A_FZ) * as + zb + S.off[(row + R) * G::RW + CX + 4 * j]);
+                }
+            } else {
+                for (int e = tid; e < G::RA; e += NT) {
+                    const size_t g = zb + S.off[e];
+#pragma unroll
+                    for (int f = 0; f < RF_N; ++f) cp_async4(&S.ring[s][f][e], src[f] + g);
+                }
+                cp_async4(&S.cring[s][0][tid], aux + A_FZ * as + zb + coff);
+                cp_async4(&S.cring[s][1][tid], aux + A_GZ * as + zb + coff);
             }
-            cp_async4(&S.cring[s][0][tid], aux + A_FZ * as + zb + coff);
-            cp_async4(&S.cring[s][1][tid], aux + A_GZ * as + zb + coff);
             cp_commit();
         }
     };
     auto wait_plane = [&](int L) {
         if (use_tma) {
             const int s = ((L % G::NS) + G::NS) % G::NS;
-            if (!bar_wait(smem_u32(&S.bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
+            if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
             phase ^= 1u << s;
         } else {
             cp_wait<PF - 1>();
@@ -418,9 +457,16 @@ __global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a
         const size_t i = (size_t)zo * plane + coff;
         // FP64 accumulator of this point: issue the loads before the plane work
         double Ui[5];
+        float divc;
+        if (PERSIST) {
 #pragma unroll
-        for (int m = 0; m < 5; ++m) Ui[m] = a.U_in[m * a.u_stride + i];
-        const float divc = aux[A_DIV * as + i];
+            for (int m = 0; m < 5; ++m) Ui[m] = __ldcg(a.U_in + m * a.u_stride + i);
+            divc = __ldcg(aux + A_DIV * as + i);
+        } else {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) Ui[m] = a.U_in[m * a.u_stride + i];
+            divc = aux[A_DIV * as + i];
+        }
         // point-wise fields of the output plane over the rectangle
         for (int e = tid; e < G::RA; e += NT) {
             const float rho = S.ring[so][RF_RHO][e], m0 = S.ring[so][RF_M0][e], m1 = S.ring[so][RF_M1][e],
@@ -478,6 +524,22 @@ __global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a
         }
     }
     cp_wait<0>();
+    __syncthreads();  // the ring may be refilled by the caller's next tile
+}
+
+template <int R>
+__global__ void __launch_bounds__(NT, (R <= 2) ? 2 : 1) k_zrhs(const StageArgs a, int zchunk,
+                                                                const __grid_constant__ ZTma tm) {
+    using G = Geo<R>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    RhsSmem<R> &S = *reinterpret_cast<RhsSmem<R> *>(smem_raw);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < G::NS; ++s) bar_init(smem_u32(&S.bars[s]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t phase = 0;
+    const int z0 = blockIdx.z * zchunk;
+    zrhs_body<R, false>(a, tm, blockIdx.x * TX, blockIdx.y * TY, z0, min(z0 + zchunk, a.d.nz), S, S.bars, phase);
 }
 
 template <int R>

@@ -77,6 +77,47 @@ def test_batch_fp32_close_to_oracle(osb, order):
             assert np.linalg.norm((Q[m] - Qo[m]).ravel()) / scale < 1e-5
 
 
+def test_batch_fp32_zmarch_items_match_per_grid_steps(osb):
+    """FP32 ensembles whose x extents are multiples of 4 run z-march items in
+    the persistent kernel; per point they do the arithmetic of the per-grid
+    z-march stage (ragged x and y tiles included).  The compiler may pair
+    multiplies and adds into FMAs differently in the two instantiations, so the
+    states agree to a few FP32 roundings of the stage residual (relative 1e-7),
+    far below the FP32 bound against the oracle (1e-5) and far below what a
+    stale or racing read of a neighbour tile would leave (>= 1e-4)."""
+    specs = [(20, 1600.0, 0.1, 2e-3), (36, 400.0, 0.2, 1.5e-3), (12, 3000.0, 0.05, 3e-3), (32, 100.0, 0.3, 1e-3)]
+    for order in (2, 4, 6, 8):
+        a = _ensemble(osb, specs, osb.OSB_FP32, order=order, seed=31)
+        b = _ensemble(osb, specs, osb.OSB_FP32, order=order, seed=31)
+        for g in a:
+            g.step(5)
+        osb.batch_step(b, 2)
+        osb.batch_step(b, 3)
+        for ga, gb in zip(a, b):
+            A, B = ga.get_state(), gb.get_state()
+            mnorm = np.linalg.norm(A[1:4].ravel())
+            for m in range(5):
+                scale = mnorm if 1 <= m <= 3 else np.linalg.norm(A[m].ravel())
+                assert np.linalg.norm((A[m] - B[m]).ravel()) / scale < 1e-7, (order, m)
+            assert gb.diagnostics()["step"] == 5
+
+
+def test_batch_fp32_unaligned_extent_uses_point_items(osb):
+    """An x extent that is not a multiple of 4 sends the whole FP32 ensemble to
+    the three-kernel items; the result still meets the FP32 bound."""
+    specs = [(18, 800.0, 0.15, 2e-3), (16, 1600.0, 0.1, 1e-3)]
+    grids = _ensemble(osb, specs, osb.OSB_FP32, order=4, seed=41)
+    osb.batch_step(grids, 4)
+    for i, ((n, Re, M, dt), g) in enumerate(zip(specs, grids)):
+        case = orc.Case(n, n, n, order=4, Re=Re, Mach=M, dt=dt)
+        Qo = orc.rk3_step(case, orc.tgv_init(case, inputs.gaussian_noise(n, n, n, 41 + i), 1e-3), 4)
+        Q = g.get_state()
+        mnorm = np.linalg.norm(Qo[1:4].ravel())
+        for m in range(5):
+            scale = mnorm if 1 <= m <= 3 else np.linalg.norm(Qo[m].ravel())
+            assert np.linalg.norm((Q[m] - Qo[m]).ravel()) / scale < 1e-5
+
+
 def test_batch_fp64_matches_oracle(osb):
     specs = [(12, 500.0, 0.2, 2e-3), (16, 1600.0, 0.1, 2e-3)]
     grids = _ensemble(osb, specs, osb.OSB_FP64, order=6, seed=21)
@@ -109,6 +150,22 @@ def test_batch_wait_limit_reports_timeout_and_context_survives(osb):
         assert np.array_equal(a.get_state(), b.get_state())
 
 
+def test_batch_fp32_zmarch_wait_limit_reports_timeout(osb):
+    grids = _ensemble(osb, [(16, 1600.0, 0.1, 2e-3), (24, 400.0, 0.2, 1e-3)], osb.OSB_FP32)
+    osb.batch_configure(0.05, True)
+    try:
+        with pytest.raises(osb.OsbError) as ei:
+            osb.batch_step(grids, 2)
+        assert ei.value.status == 5
+    finally:
+        osb.batch_configure(2.0, False)
+    fresh = _ensemble(osb, [(16, 1600.0, 0.1, 2e-3)], osb.OSB_FP32)
+    ref = _ensemble(osb, [(16, 1600.0, 0.1, 2e-3)], osb.OSB_FP32)
+    osb.batch_step(fresh, 2)
+    ref[0].step(2)
+    assert np.array_equal(fresh[0].get_state(), ref[0].get_state())
+
+
 def test_batch_rejects_mixed_configurations(osb):
     a = osb.Grid(osb.Config(8, 8, 8, order=4))
     b = osb.Grid(osb.Config(8, 8, 8, order=8))
@@ -130,3 +187,11 @@ def test_autotune_restores_state(osb, tmp_path, monkeypatch):
     d1 = g.diagnostics()
     assert d1["step"] == d0["step"] and d1["t"] == d0["t"]
     g.step(1)  # still usable
+
+
+def test_autotune_fp32_candidates(osb):
+    g = _ensemble(osb, [(32, 1600.0, 0.1, 1e-3)], osb.OSB_FP32)[0]
+    before = g.get_state()
+    tz = osb.autotune(g, trial_steps=2)
+    assert tz in (4, 8, 16, 32)
+    assert np.array_equal(g.get_state(), before)
