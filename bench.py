@@ -80,9 +80,22 @@ def stage_flops_per_point(r: int) -> dict:
 
 ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}  # fused minimum per point-stage
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# launch list of the same workload (profiles/launches_tgv256_o4_fp64.md).
+# An entry is removed whenever its kernel changes; the key is the workload
+# name bench.py reports.
+TRAFFIC_PER_LAUNCH = {
+    ("tgv_256^3_order4_fp64", "k_resid"): 4.610e9,
+}
+
+# FP64 peak from unit counts and clocks: 2 DFMA thread-instructions per SM per
+# cycle (ncu peak_sustained of sm__sass_thread_inst_executed_op_dfma_pred_on),
+# 2 flops each, 152 SMs, 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+
 
 def peaks():
-    p = dict(hbm_gbs=None, fp64_tflops=1.25, fp32_tflops=None, src="fallback")
+    p = dict(hbm_gbs=None, fp64_tflops=FP64_PEAK_TFLOPS, fp32_tflops=None, src="fallback")
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
@@ -341,13 +354,15 @@ def run_ours(args):
     if w["precision"] == "fp64":
         achieved = fl["resid"] * npts / (avg_ms * 1e-3) / 1e12
         roof = {"kernel": "k_resid", "bound": "alu", "achieved": achieved, "peak": pk["fp64_tflops"],
-                "unit": "TFLOP/s", "frac": achieved / pk["fp64_tflops"], "traffic": None,
-                "peak_src": "nominal FP64 rate of GB300 (1.25 TFLOP/s), not measured here",
+                "unit": "TFLOP/s", "frac": achieved / pk["fp64_tflops"],
+                "traffic": TRAFFIC_PER_LAUNCH.get((w["workload"], "k_resid")),
+                "peak_src": "FP64 FMA rate from unit counts and clock: 2 DFMA/SM/cycle x 2 flops x 152 SMs x 2070 MHz",
                 "flops_per_point": fl["resid"]}
     else:
         achieved = ALG_BYTES["fp32"] * npts / (avg_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_resid", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"], "traffic": None,
+        roof = {"kernel": "k_zrhs", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                "traffic": TRAFFIC_PER_LAUNCH.get((w["workload"], "k_zrhs")),
                 "peak_src": pk["src"]}
     kernel_ms = {k: v["total_ms"] / max(v["launches"], 1) for k, v in prof.items()}
     stage_ms = sum(kernel_ms.values())

@@ -531,6 +531,7 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     qout[2] = nullptr;
     a.src = src[k];
     a.src_is_f64 = !f32;
+    a.src_is_u32 = f32 && k == 0;
     a.src_stride = (k == 0 && !f32) ? g->u_stride : g->q_stride;
     a.U_in = (k == 0) ? Ucur : Unext;
     a.U_out = Unext;

@@ -71,6 +71,7 @@ struct StageArgs {
     int visc_form;          // OSB_VISC_A / OSB_VISC_B
     const void *src;        // stencil source q_{k-1}
     int src_is_f64;         // 1: src holds doubles (U register), 0: type T
+    int src_is_u32;         // FP32 path: src is the rounded FP32 copy of U_in (src = d2f(U_in) at every point)
     size_t src_stride;      // elements between fields of src
     void *aux;              // NAUX fields of type T
     size_t aux_stride;

@@ -29,6 +29,8 @@
 // term (the product rule applied to d_j(u_i tau_ij)).
 #pragma once
 
+#include <string.h>
+
 #include "osb_internal.cuh"
 
 namespace osb {
@@ -109,34 +111,65 @@ __device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R> &nb, const
 // Exact float -> double and round-to-nearest-even double -> float, on the
 // integer pipes (GB300 issues FP64 instructions, conversions included, at
 // 1/64 of the FP32 rate).  Values below the smallest normal float are flushed
-// to signed zero; infinities and NaNs are kept.
-__device__ __forceinline__ double f2d_bits(float f) {
-    const uint32_t b = __float_as_uint(f);
-    const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
-    const uint32_t e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
-    uint64_t r;
-    if (e == 0xffu)
-        r = sign | 0x7ff0000000000000ull | ((uint64_t)m << 29);
-    else if (e == 0u)
-        r = sign;
-    else
-        r = sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
-    return __longlong_as_double((long long)r);
+// to signed zero; infinities and NaNs are kept.  Branch-free:
+// the special cases are selects, so a warp never diverges here.
+__host__ __device__ __forceinline__ uint32_t fbits(float f) {
+#ifdef __CUDA_ARCH__
+    return __float_as_uint(f);
+#else
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+#endif
+}
+__host__ __device__ __forceinline__ float bitsf(uint32_t u) {
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(u);
+#else
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+#endif
 }
 
-__device__ __forceinline__ float d2f_bits(double d) {
+__host__ __device__ __forceinline__ double f2d_bits(float f) {
+    const uint32_t b = fbits(f), sign = b & 0x80000000u, a = b & 0x7fffffffu;
+    // exponent rebias 127 -> 1023 is + (896 << 20) on the high word; for
+    // infinities and NaNs the exponent field goes from 0xff to 0x7ff instead
+    uint32_t hi = (a >> 3) + (a >= 0x7f800000u ? 0x70000000u : 0x38000000u);
+    uint32_t lo = b << 29;
+    const bool tiny = a < 0x00800000u;  // zero or denormal
+    hi = tiny ? 0u : hi;
+    lo = tiny ? 0u : lo;
+    const uint64_t r = ((uint64_t)(sign | hi) << 32) | lo;
+#ifdef __CUDA_ARCH__
+    return __longlong_as_double((long long)r);
+#else
+    double d;
+    memcpy(&d, &r, 8);
+    return d;
+#endif
+}
+
+__host__ __device__ __forceinline__ float d2f_bits(double d) {
+#ifdef __CUDA_ARCH__
     const uint64_t b = (uint64_t)__double_as_longlong(d);
-    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7ffu);
-    const uint64_t m = b & 0xfffffffffffffull;
-    if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x400000u : 0u));
-    const int fe = e - 1023 + 127;
-    if (fe >= 0xff) return __uint_as_float(sign | 0x7f800000u);
-    if (fe <= 0) return __uint_as_float(sign);
-    const uint32_t hi = (uint32_t)(m >> 29), lo = (uint32_t)(m & 0x1fffffffu);
-    uint32_t f = ((uint32_t)fe << 23) | hi;
-    if (lo > 0x10000000u || (lo == 0x10000000u && (hi & 1u))) f += 1u;  // carry into the exponent is correct
-    return __uint_as_float(sign | f);
+#else
+    uint64_t b;
+    memcpy(&b, &d, 8);
+#endif
+    const uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+    const uint32_t sign = hw & 0x80000000u, ah = hw & 0x7fffffffu;
+    // normal range: exponent 1023 -> 127 and the top 23 mantissa bits
+    const uint32_t f = ((ah - 0x38000000u) << 3) | (lw >> 29);
+    // round to nearest, ties to even, on the 29 dropped bits (a carry into
+    // the exponent is correct, up to infinity)
+    const uint32_t inc = ((lw & 0x1fffffffu) + (f & 1u) + 0x0fffffffu) >> 29;
+    uint32_t r = sign | (f + inc);
+    r = ah < 0x38100000u ? sign : r;  // below the smallest normal float
+    const uint32_t nan = (ah > 0x7ff00000u || (ah == 0x7ff00000u && lw != 0u)) ? 0x400000u : 0u;
+    r = ah >= 0x47f00000u ? (sign | 0x7f800000u | nan) : r;  // overflow, infinity, NaN
+    return bitsf(r);
 }
 
 // ---------------------------------------------------------------------------

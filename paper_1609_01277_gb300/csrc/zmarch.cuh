@@ -23,6 +23,8 @@
 #include <cuda.h>
 #include <stddef.h>
 
+#include <type_traits>
+
 #include "stage.cuh"
 
 namespace osb {
@@ -514,13 +516,22 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
             for (int m = 0; m < 5; ++m) res[m] += a.closure[(size_t)m * d.n + i];
         }
         if (active) {
+            // stage value q = float(U_in) + alpha dt R; in the first stage the
+            // stencil source is the FP32 copy of U_in, so float(U_in) is the
+            // queue centre and needs no conversion
+            auto update = [&](auto from_src) {
 #pragma unroll
-            for (int m = 0; m < 5; ++m) {
-                const double Un = Ui[m] + f2d_bits(bdt * res[m]);
-                a.U_out[m * a.u_stride + i] = Un;
-                if (qo) qo[m * a.q_stride + i] = fmaf(adt, res[m], d2f_bits(Ui[m]));
-                if (cp) cp[m * a.q_stride + i] = d2f_bits(Un);
-            }
+                for (int m = 0; m < 5; ++m) {
+                    const double Un = Ui[m] + f2d_bits(bdt * res[m]);
+                    a.U_out[m * a.u_stride + i] = Un;
+                    if (qo) qo[m * a.q_stride + i] = fmaf(adt, res[m], decltype(from_src)::value ? qQ[m][R] : d2f_bits(Ui[m]));
+                    if (cp) cp[m * a.q_stride + i] = d2f_bits(Un);
+                }
+            };
+            if (a.src_is_u32)
+                update(std::true_type{});
+            else
+                update(std::false_type{});
         }
     }
     cp_wait<0>();
