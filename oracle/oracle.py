@@ -36,7 +36,7 @@ class _Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("order", ctypes.c_int), ("visc_form", ctypes.c_int),
                 ("Re", ctypes.c_double), ("Mach", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("Pr", ctypes.c_double), ("dt", ctypes.c_double)]
+                ("Pr", ctypes.c_double), ("dt", ctypes.c_double), ("nz_domain", ctypes.c_int)]
 
 
 _lib = None
@@ -83,10 +83,11 @@ class Case:
     gamma: float = 1.4
     Pr: float = 0.71
     dt: float = 3.385e-3
+    nz_domain: int = 0  # z-slab of a periodic grid with this many planes (0: the array is the grid)
 
     def c(self) -> _Grid:
         return _Grid(self.nx, self.ny, self.nz, self.order, self.visc_form,
-                     self.Re, self.Mach, self.gamma, self.Pr, self.dt)
+                     self.Re, self.Mach, self.gamma, self.Pr, self.dt, self.nz_domain)
 
     @property
     def shape(self):

@@ -48,6 +48,8 @@ typedef struct {
     int order;      /* even, 2..12 */
     int visc_form;  /* 0 = form A (conservative), 1 = form B (product rule) */
     double Re, Mach, gamma, Pr, dt;
+    int nz_domain;  /* points per 2 pi along z when the array is a z-slab of a
+                       larger periodic grid (ghost planes included); 0: nz */
 } orc_grid;
 
 /* ------------------------------------------------------------------------ */
@@ -119,7 +121,7 @@ static inline size_t npts(const orc_grid *g) {
 }
 
 static double spacing(const orc_grid *g, int axis) {
-    int n = axis == 0 ? g->nx : (axis == 1 ? g->ny : g->nz);
+    int n = axis == 0 ? g->nx : (axis == 1 ? g->ny : (g->nz_domain > 0 ? g->nz_domain : g->nz));
     return 2.0 * M_PI / (double)n;
 }
 
