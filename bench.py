@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
-    ap.add_argument("--ensemble-steps", type=int, default=5)
+    ap.add_argument("--ensemble-steps", type=int, default=20)
     ap.add_argument("--no-closure", action="store_true")
     return ap.parse_args()
 
@@ -81,11 +81,12 @@ def stage_flops_per_point(r: int) -> dict:
 ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}  # fused minimum per point-stage
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# launch list of the same workload (profiles/launches_tgv256_o4_fp64.md).
+# launch list of the same workload (profiles/launches_tgv256_o4_*.md).
 # An entry is removed whenever its kernel changes; the key is the workload
 # name bench.py reports.
 TRAFFIC_PER_LAUNCH = {
     ("tgv_256^3_order4_fp64", "k_resid"): 4.610e9,
+    ("tgv_256^3_order4_fp32", "k_zrhs"): 2.4776e9,   # profiles/launches_tgv256_o4_fp32.md
 }
 
 # FP64 peak from unit counts and clocks: 2 DFMA thread-instructions per SM per
@@ -303,7 +304,9 @@ def run_ensemble(torch, osb, inputs, steps, precision):
     return {"instances": len(specs), "points": pts, "steps": steps, "tile_depth": tuned,
             "value": steps * 3 * pts / t_batch, "ms_per_step": 1e3 * t_batch / steps,
             "per_grid_launch_value": steps * 3 * pts / t_seq, "speedup_vs_per_grid_launches": t_seq / t_batch,
-            "ke_first4": ke, "launches_per_step": 1, "per_grid_launches_per_step": 9 * len(specs)}
+            "ke_first4": ke, "launches_per_step": 1,
+            "per_grid_launches_per_step": (9 if precision == "fp64" else 6) * len(specs),
+            "items": "three-kernel point items" if precision == "fp64" else "z-march column items"}
 
 
 def run_ours(args):
