@@ -1,0 +1,157 @@
+"""Long Taylor-Green runs on the GPU (Section 3.3): the kinetic energy E_k(t),
+the enstrophy and the dissipation rate eps = -dE_k/dt of the FP64 and FP32
+paths, the KE-decay error of FP32 against FP64, and the per-field state error
+of FP32 against FP64 after a fixed number of steps.
+
+Every step runs in the library's kernels; this module only drives grids and
+reads their FP64 diagnostics.  CLI:
+
+    python -m paper_1609_01277_gb300.experiments curves --n 256 --order 4 --t-end 20
+    python -m paper_1609_01277_gb300.experiments fp32-error --n 512 --order 8 --steps 200
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+DT_64 = 3.385e-3  # time step of the 64^3 case (Section 3.3); halved per doubling of N
+
+
+def default_dt(n: int) -> float:
+    return DT_64 * 64.0 / n
+
+
+def _grid(osb, torch, n, order, precision, dt, seed, amp, Re=1600.0, Mach=0.1):
+    from . import inputs
+    cfg = osb.Config(n, n, n, order=order, precision=precision, Re=Re, Mach=Mach, dt=dt)
+    g = osb.Grid(cfg)
+    noise = torch.from_numpy(inputs.gaussian_noise(n, n, n, seed)).cuda() if amp > 0 else None
+    g.init_taylor_green(noise, amp)
+    return g
+
+
+def tgv_curves(n: int, order: int, precision: str, t_end: float, every: int = 50, dt: float | None = None,
+               seed: int = 1234, amp: float = 1e-4) -> dict:
+    """E_k, enstrophy and max CFL every `every` steps up to t_end."""
+    import torch
+    from . import osb
+    osb.load()
+    dt = dt or default_dt(n)
+    prec = osb.OSB_FP64 if precision == "fp64" else osb.OSB_FP32
+    g = _grid(osb, torch, n, order, prec, dt, seed, amp)
+    nsteps = int(round(t_end / dt))
+    t, ke, ens, cfl = [], [], [], []
+    d = g.diagnostics()
+    t.append(d["t"]), ke.append(d["ke"]), ens.append(d["enstrophy"]), cfl.append(d["max_cfl"])
+    done = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    while done < nsteps:
+        k = min(every, nsteps - done)
+        g.step(k)
+        done += k
+        d = g.diagnostics()
+        t.append(d["t"]), ke.append(d["ke"]), ens.append(d["enstrophy"]), cfl.append(d["max_cfl"])
+    seconds = time.perf_counter() - t0
+    del g
+    torch.cuda.empty_cache()
+    return dict(n=n, order=order, precision=precision, dt=dt, steps=nsteps, every=every, t=t, ke=ke,
+                enstrophy=ens, max_cfl=cfl, seconds=seconds, point_stages_per_s=3.0 * n ** 3 * nsteps / seconds)
+
+
+def dissipation(t, ke):
+    """eps = -dE_k/dt by second-order central differences (one-sided at the ends)."""
+    t, ke = np.asarray(t), np.asarray(ke)
+    return -np.gradient(ke, t)
+
+
+def summarize(c: dict) -> dict:
+    t, ke, ens = np.asarray(c["t"]), np.asarray(c["ke"]), np.asarray(c["enstrophy"])
+    eps = dissipation(t, ke)
+    i_eps, i_ens = int(np.argmax(eps)), int(np.argmax(ens))
+    at = {}
+    for tt in (0.0, 3.0, 5.0, 9.0, 10.0, 15.0, 20.0):
+        if tt <= t[-1] + 1e-9:
+            j = int(np.argmin(np.abs(t - tt)))
+            at[f"{tt:g}"] = dict(ke=float(ke[j]), eps=float(eps[j]), enstrophy=float(ens[j]),
+                                 two_over_re_enstrophy=float(2.0 / 1600.0 * ens[j]))
+    return dict(n=c["n"], order=c["order"], precision=c["precision"], steps=c["steps"], dt=c["dt"],
+                seconds=c["seconds"], point_stages_per_s=c["point_stages_per_s"],
+                ke_drop_by_t3=float(1.0 - ke[int(np.argmin(np.abs(t - 3.0)))] / ke[0]) if t[-1] >= 3 else None,
+                t_max_dissipation=float(t[i_eps]), max_dissipation=float(eps[i_eps]),
+                t_max_enstrophy=float(t[i_ens]), max_enstrophy=float(ens[i_ens]),
+                max_cfl=float(np.max(c["max_cfl"])), at=at)
+
+
+def compare_curves(a: dict, ref: dict) -> dict:
+    """KE-decay error of run a against the reference run: max_t |E_k - E_k^ref| / E_k^ref(0),
+    and the same for the dissipation rate relative to its peak."""
+    ka, kr = np.asarray(a["ke"]), np.asarray(ref["ke"])
+    ea, er = dissipation(a["t"], ka), dissipation(ref["t"], kr)
+    return dict(ke_err=float(np.max(np.abs(ka - kr)) / kr[0]),
+                eps_err=float(np.max(np.abs(ea - er)) / np.max(np.abs(er))),
+                speedup=ref["seconds"] / a["seconds"])
+
+
+def fp32_error(n: int, order: int, steps: int, dt: float | None = None, seed: int = 1234, amp: float = 1e-4) -> dict:
+    """Relative L2 error of every conserved field of the FP32 path against the
+    FP64 path after `steps` steps from the same state (momentum fields relative
+    to the norm of the whole momentum, which starts with rho w = 0)."""
+    import torch
+    from . import osb
+    osb.load()
+    dt = dt or default_dt(n)
+    out = {}
+    states = {}
+    for name, prec in (("fp64", osb.OSB_FP64), ("fp32", osb.OSB_FP32)):
+        g = _grid(osb, torch, n, order, prec, dt, seed, amp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(steps)
+        torch.cuda.synchronize()
+        out[f"{name}_seconds"] = time.perf_counter() - t0
+        states[name] = g.get_state_device()
+        del g
+    a, b = states["fp32"], states["fp64"]
+    mnorm = float(torch.linalg.vector_norm(b[1:4]))
+    names = ("rho", "rho_u", "rho_v", "rho_w", "rho_E")
+    for m in range(5):
+        scale = mnorm if 1 <= m <= 3 else float(torch.linalg.vector_norm(b[m]))
+        out[f"rel_l2_{names[m]}"] = float(torch.linalg.vector_norm(a[m] - b[m])) / scale
+    out.update(n=n, order=order, steps=steps, dt=dt)
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("curves")
+    c.add_argument("--n", type=int, default=256)
+    c.add_argument("--order", type=int, default=4)
+    c.add_argument("--t-end", type=float, default=20.0)
+    c.add_argument("--every", type=int, default=50)
+    c.add_argument("--precisions", default="fp64,fp32")
+    c.add_argument("--curves-out", default=None, help="write the full curves as JSON here")
+    e = sub.add_parser("fp32-error")
+    e.add_argument("--n", type=int, default=512)
+    e.add_argument("--order", type=int, default=8)
+    e.add_argument("--steps", type=int, default=200)
+    args = ap.parse_args(argv)
+    if args.cmd == "curves":
+        runs = {p: tgv_curves(args.n, args.order, p, args.t_end, args.every) for p in args.precisions.split(",")}
+        res = {p: summarize(r) for p, r in runs.items()}
+        if "fp64" in runs and "fp32" in runs:
+            res["fp32_vs_fp64"] = compare_curves(runs["fp32"], runs["fp64"])
+        if args.curves_out:
+            with open(args.curves_out, "w") as f:
+                json.dump(runs, f)
+        print(json.dumps(res))
+    else:
+        print(json.dumps(fp32_error(args.n, args.order, args.steps)))
+
+
+if __name__ == "__main__":
+    main()
