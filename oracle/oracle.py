@@ -57,6 +57,7 @@ def lib():
         _lib.orc_rk3_step.argtypes = [g, d, ctypes.c_int]
         _lib.orc_rk3_coeffs.argtypes = [d, d]
         _lib.orc_rk3_linear.argtypes = [ctypes.c_size_t, d, d, ctypes.c_int, ctypes.c_double]
+        _lib.orc_scalar_rk3.argtypes = [g, d, ctypes.c_double, d, d, ctypes.c_int]
         _lib.orc_tgv_init.argtypes = [g, d, ctypes.c_double, d]
         _lib.orc_diagnostics.argtypes = [g, d, d]
         _lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -169,6 +170,23 @@ def rk3_linear(lam: np.ndarray, y0: np.ndarray, nsteps: int, dt: float) -> np.nd
     lam = np.ascontiguousarray(lam, dtype=np.float64)
     y = np.array(y0, dtype=np.float64, order="C")
     lib().orc_rk3_linear(lam.size, _p(lam), _p(y), int(nsteps), float(dt))
+    return y
+
+
+def scalar_rk3(case: Case, phi: np.ndarray, adv=(0.0, 0.0, 0.0), k: float = 0.0, S: np.ndarray | None = None,
+               nsteps: int = 1) -> np.ndarray:
+    """Scalar advection-diffusion d phi/dt = -a_j D_j phi + k L_j phi - S
+    (Sections 3.1 and 3.2) advanced nsteps RK3 steps of case.dt; phi and S are
+    (nz, ny, nx) float64 arrays."""
+    y = np.ascontiguousarray(phi, dtype=np.float64).reshape(case.shape).copy()
+    a = np.ascontiguousarray(adv, dtype=np.float64)
+    Sp = None
+    if S is not None:
+        S = np.ascontiguousarray(S, dtype=np.float64).reshape(case.shape)
+        Sp = _p(S)
+    g = case.c()
+    if lib().orc_scalar_rk3(ctypes.byref(g), _p(a), float(k), Sp, _p(y), int(nsteps)) != 0:
+        raise MemoryError("orc_scalar_rk3")
     return y
 
 
