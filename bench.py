@@ -309,6 +309,34 @@ def run_ensemble(torch, osb, inputs, steps, precision):
             "items": "three-kernel point items" if precision == "fp64" else "z-march column items"}
 
 
+def run_scalar(torch, osb, n, order, steps, warmup, peak):
+    """Scalar advection-diffusion (the paper's Sections 3.1-3.2 equation) on a
+    3D periodic grid: point-stages/s and the FP64 roofline of its one kernel
+    (per point-stage 2 FMAs per tap on 3 axes, the centre multiply, the source
+    and the two RK FMAs: 12 r + 6 flops)."""
+    r = order // 2
+    g = torch.Generator(device="cpu").manual_seed(11)
+    phi = torch.randn((n, n, n), generator=g, dtype=torch.float64).cuda()
+    src = torch.randn((n, n, n), generator=g, dtype=torch.float64).cuda()
+    work = torch.empty(2 * n ** 3, dtype=torch.float64, device="cuda")
+    adv, k, dt = (1.0, -0.5, 0.25), 0.75, 1e-4
+    osb.scalar_rk3(phi, work, order, adv, k, dt, warmup, src)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    osb.scalar_rk3(phi, work, order, adv, k, dt, steps, src)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    flops = (12 * r + 6) * 3 * n ** 3 * steps
+    del phi, src, work
+    torch.cuda.empty_cache()
+    return {"value": 3 * n ** 3 * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "fp64_tflops": flops / (ms * 1e-3) / 1e12, "fp64_frac": flops / (ms * 1e-3) / 1e12 / peak,
+            "hbm_gbs_min_traffic": 40 * 3 * n ** 3 * steps / (ms * 1e-3) / 1e9,
+            "flops_per_point_stage": 12 * r + 6, "steps": steps}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -435,6 +463,10 @@ def run_ours(args):
         e64, e32 = variants["ensemble64_order4_fp64"], variants["ensemble64_order4_fp32"]
         e32["speedup_vs_fp64_ensemble"] = e32["value"] / e64["value"]
         e32["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(e32["ke_first4"], e64["ke_first4"]))
+
+    if not args.no_variants and world == 1:
+        variants["scalar_advdiff_256^3_order8_fp64"] = run_scalar(torch, osb, n=256, order=8, steps=args.steps,
+                                                                  warmup=args.warmup, peak=pk["fp64_tflops"])
 
     if not args.no_closure and world == 1:
         from paper_1609_01277_gb300 import closure as clo

@@ -212,6 +212,33 @@ osb_status osb_diagnostics_noalloc(const double *Q_dev, int nx, int ny, int nz, 
                                    const osb_params *params, double *out_dev, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Scalar advection-diffusion on the periodic box [0, 2 pi)^3: the equation of
+ * the paper's verification tests -- the wave equation of Section 3.1
+ * (k = 0, no source) and the manufactured-solution advection-diffusion test
+ * of Section 3.2:
+ *     d phi/dt + d_j(phi a_j - k d_j phi) + S = 0,   a_j, k constant,
+ * discretised with the central first- and second-derivative stencils of the
+ * given order (Section 2.4, h = 2 pi / n per axis; an axis with one point
+ * carries no derivative) and advanced nsteps steps of the low-storage RK3
+ * scheme used by osb_rk3_step.  FP64 throughout.
+ *
+ *  phi_dev:  device, nx*ny*nz FP64 values, x fastest; read as phi(t), written
+ *            with phi(t + nsteps dt).  Caller-owned.
+ *  work_dev: device scratch of 2*nx*ny*nz FP64 values, caller-owned, clobbered.
+ *  src_dev:  device, nx*ny*nz FP64 values of S, or NULL for S = 0.
+ *  adv:      host, the 3 velocity components a_0, a_1, a_2.
+ *  diff:     the diffusivity k >= 0.
+ *  cuda_stream: the stream the kernels (and, for odd nsteps, one device-to-
+ *            device copy of the result) are queued on; the call does not
+ *            synchronise and allocates nothing.
+ * Errors: NULL pointers, sizes below 1 or above 2^31 points, an order outside
+ * 2..12 or odd, dt <= 0, k < 0 or nsteps < 0 -> OSB_ERR_INVALID_ARG; buffers
+ * not 8-byte aligned -> OSB_ERR_BUFFER; a failed launch -> OSB_ERR_CUDA.
+ * nsteps = 0 does nothing. */
+osb_status osb_scalar_rk3(double *phi_dev, double *work_dev, const double *src_dev, int nx, int ny, int nz,
+                          int order, const double *adv, double diff, double dt, int nsteps, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Learned residual correction ("closure") for coarse grids.  Not in the paper
  * (its future work lists LES models, Section 1); a spec extension.
  * Network: three 3x3x3 periodic convolutions 5 -> 32 -> 32 -> 5 with ReLU

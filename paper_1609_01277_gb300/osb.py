@@ -31,7 +31,7 @@ EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_gri
            "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_closure_create", "osb_closure_destroy",
            "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_status", "osb_closure_sync_weights",
            "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
-           "osb_box_filter", "osb_profile_start", "osb_profile_stop",
+           "osb_box_filter", "osb_scalar_rk3", "osb_profile_start", "osb_profile_stop",
            "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
@@ -90,6 +90,8 @@ def load(path: str | None = None):
     L.osb_batch_configure.argtypes = [ctypes.c_double, ctypes.c_int]
     L.osb_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.osb_diagnostics_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, vp, vp]
+    L.osb_scalar_rk3.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                 ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     L.osb_profile_start.argtypes = [vp, ctypes.c_int]
     L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.osb_status_string.argtypes = [ctypes.c_int]
@@ -248,6 +250,28 @@ def diagnostics_noalloc(Q_dev, cfg: Config, out_dev, stream=None) -> None:
     p = cfg.params()
     check(load().osb_diagnostics_noalloc(Q_dev.data_ptr(), cfg.nx, cfg.ny, cfg.nz, cfg.order, ctypes.byref(p),
                                          out_dev.data_ptr(), st.cuda_stream), "osb_diagnostics_noalloc")
+
+
+def scalar_rk3(phi, work, order: int, adv=(0.0, 0.0, 0.0), diff: float = 0.0, dt: float = 1e-3,
+               nsteps: int = 1, src=None, stream=None) -> None:
+    """Advance the scalar field phi (a (nz, ny, nx) float64 CUDA tensor, in place)
+    by nsteps RK3 steps of d phi/dt = -a_j D_j phi + k L_j phi - S on the
+    periodic box [0, 2 pi)^3 (paper Sections 3.1-3.2).  work: a CUDA float64
+    tensor of at least 2 * phi.numel() values; src: None or a tensor like phi."""
+    import torch
+    if phi.dtype != torch.float64 or not phi.is_cuda or not phi.is_contiguous() or phi.dim() != 3:
+        raise ValueError("phi must be a contiguous (nz, ny, nx) float64 CUDA tensor")
+    if work.dtype != torch.float64 or not work.is_cuda or work.numel() < 2 * phi.numel():
+        raise ValueError("work must be a float64 CUDA tensor of 2 * phi.numel() values")
+    if src is not None and (src.dtype != torch.float64 or not src.is_cuda or src.shape != phi.shape
+                            or not src.is_contiguous()):
+        raise ValueError("src must be a contiguous float64 CUDA tensor shaped like phi")
+    st = stream if stream is not None else torch.cuda.current_stream()
+    nz, ny, nx = phi.shape
+    a = (ctypes.c_double * 3)(*[float(v) for v in adv])
+    check(load().osb_scalar_rk3(phi.data_ptr(), work.data_ptr(), None if src is None else src.data_ptr(),
+                                nx, ny, nz, int(order), a, float(diff), float(dt), int(nsteps), st.cuda_stream),
+          "osb_scalar_rk3")
 
 
 def batch_step(grids, nsteps: int) -> None:

@@ -127,3 +127,18 @@ def test_noalloc_diagnostics_rejects_bad_arguments_before_gpu_work(osb):
     assert b"too large" in L.osb_last_error()
     bad = osb.Params(1600, 0.1, 1.0, 0.71, 1e-3)
     assert L.osb_diagnostics_noalloc(ok_ptr, 8, 8, 8, 4, ctypes.byref(bad), ok_ptr, None) == 1
+
+
+def test_scalar_rejects_bad_arguments_before_gpu_work(osb):
+    L = osb.load()
+    a = (ctypes.c_double * 3)(1.0, 0.0, 0.0)
+    ok = 4096  # never dereferenced: every call below fails its argument checks
+    assert L.osb_scalar_rk3(None, ok, None, 8, 8, 8, 4, a, 0.1, 1e-3, 1, None) == 1
+    assert L.osb_scalar_rk3(ok, ok, None, 0, 8, 8, 4, a, 0.1, 1e-3, 1, None) == 1
+    assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 3, a, 0.1, 1e-3, 1, None) == 1
+    assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 14, a, 0.1, 1e-3, 1, None) == 1
+    assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 4, a, -0.1, 1e-3, 1, None) == 1
+    assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 4, a, 0.1, 0.0, 1, None) == 1
+    assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 4, a, 0.1, 1e-3, -1, None) == 1
+    assert L.osb_scalar_rk3(ok + 4, ok, None, 8, 8, 8, 4, a, 0.1, 1e-3, 1, None) == 6
+    assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 4, a, 0.1, 1e-3, 0, None) == 0  # nothing to do
