@@ -58,6 +58,8 @@ def lib():
         _lib.orc_rk3_coeffs.argtypes = [d, d]
         _lib.orc_rk3_linear.argtypes = [ctypes.c_size_t, d, d, ctypes.c_int, ctypes.c_double]
         _lib.orc_scalar_rk3.argtypes = [g, d, ctypes.c_double, d, d, ctypes.c_int]
+        _lib.orc_euler_step.argtypes = [g, d, ctypes.c_int]
+        _lib.orc_euler_linear.argtypes = [ctypes.c_size_t, d, d, ctypes.c_int, ctypes.c_double]
         _lib.orc_tgv_init.argtypes = [g, d, ctypes.c_double, d]
         _lib.orc_diagnostics.argtypes = [g, d, d]
         _lib.orc_set_threads.argtypes = [ctypes.c_int]
@@ -157,6 +159,22 @@ def rk3_step(case: Case, Q: np.ndarray, nsteps: int = 1) -> np.ndarray:
     if lib().orc_rk3_step(ctypes.byref(g), _p(Q), int(nsteps)) != 0:
         raise MemoryError("oracle rk3: allocation failed")
     return Q
+
+
+def euler_step(case: Case, Q: np.ndarray, nsteps: int = 1) -> np.ndarray:
+    """Forward Euler (Section 2.4): Q^{n+1} = Q^n + dt R(Q^n)."""
+    y = np.ascontiguousarray(Q, dtype=np.float64).reshape((5,) + case.shape).copy()
+    g = case.c()
+    if lib().orc_euler_step(ctypes.byref(g), _p(y), int(nsteps)) != 0:
+        raise MemoryError("orc_euler_step")
+    return y
+
+
+def euler_linear(lam: np.ndarray, y0: np.ndarray, nsteps: int, dt: float) -> np.ndarray:
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    y = np.ascontiguousarray(y0, dtype=np.float64).copy()
+    lib().orc_euler_linear(lam.size, _p(lam), _p(y), int(nsteps), float(dt))
+    return y
 
 
 def rk3_coeffs():

@@ -408,8 +408,27 @@ static int lsrk3(size_t n, double *y, int nsteps, double dt, orc_rhs_fn rhs, voi
     return 0;
 }
 
+/* Forward Euler (Section 2.4 offers it beside the RK3 scheme):
+ * y^{n+1} = y^n + dt R(y^n). */
+static int euler(size_t n, double *y, int nsteps, double dt, orc_rhs_fn rhs, void *ctx) {
+    double *R = alloc(n);
+    if (!R) return -1;
+    for (int s = 0; s < nsteps; ++s) {
+        if (rhs(ctx, y, R)) { free(R); return -1; }
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)n; ++i) y[i] = y[i] + dt * R[i];
+    }
+    free(R);
+    return 0;
+}
+
 static int ns_rhs(void *ctx, const double *y, double *r) {
     return orc_residual((const orc_grid *)ctx, y, r);
+}
+
+/* Advance the conserved state Q in place by nsteps forward-Euler steps. */
+int orc_euler_step(const orc_grid *g, double *Q, int nsteps) {
+    return euler(5 * npts(g), Q, nsteps, g->dt, ns_rhs, (void *)g);
 }
 
 /* Advance the conserved state Q (5 fields) in place by nsteps RK3 steps. */
@@ -429,6 +448,11 @@ static int lin_rhs(void *ctx, const double *y, double *r) {
 int orc_rk3_linear(size_t n, const double *lam, double *y, int nsteps, double dt) {
     lin_ctx c = {n, lam};
     return lsrk3(n, y, nsteps, dt, lin_rhs, &c);
+}
+
+int orc_euler_linear(size_t n, const double *lam, double *y, int nsteps, double dt) {
+    lin_ctx c = {n, lam};
+    return euler(n, y, nsteps, dt, lin_rhs, &c);
 }
 
 /* ------------------------------------------------------------------------ */

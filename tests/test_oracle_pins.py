@@ -285,6 +285,34 @@ def test_rk3_temporal_order_is_three():
     assert 2.9 < s1 < 3.1 and 2.9 < s2 < 3.1
 
 
+def test_forward_euler_linear_closed_form_and_first_order():
+    """Forward Euler (Section 2.4): y_n = (1 + lambda dt)^n y_0 exactly, and the
+    error against exp(lambda t) halves with dt."""
+    lam = np.array([-1.0, -3.0, 0.5, -0.1])
+    dt, nsteps = 0.1, 7
+    y = orc.euler_linear(lam, np.ones(4), nsteps, dt)
+    assert np.allclose(y, (1 + lam * dt) ** nsteps, rtol=1e-14, atol=0)
+    errs = []
+    for n in (40, 80, 160):
+        errs.append(abs(orc.euler_linear(np.array([-2.0]), np.ones(1), n, 1.0 / n)[0] - math.exp(-2.0)))
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 0.9 < math.log2(e0 / e1) < 1.1
+
+
+def test_forward_euler_conserves_totals_and_is_one_stage_of_the_residual():
+    """Each forward-Euler step adds dt R, whose totals vanish (form A), so the
+    conserved totals stay put to roundoff; and a step from the uniform state
+    leaves it unchanged (R = 0)."""
+    case = orc.Case(16, 16, 16, order=4, dt=2e-3)
+    Q = conserved(*inputs.smooth_primitive_state(16, 16, 16, seed=11), gamma=case.gamma)
+    Q1 = orc.euler_step(case, Q, 5)
+    for m in range(5):
+        assert abs(Q1[m].sum() - Q[m].sum()) <= 1e-12 * np.abs(Q[m]).sum()
+    one = np.ones(case.shape)
+    U = conserved(1.3 * one, 0.4 * one, -0.2 * one, 0.7 * one, 50.0 * one)
+    assert np.allclose(orc.euler_step(case, U, 3), U, rtol=0, atol=1e-13)
+
+
 # --------------------------------------------------------------------------
 # Taylor-Green initial state (Section 3.3)
 # --------------------------------------------------------------------------
