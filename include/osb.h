@@ -145,6 +145,14 @@ osb_status osb_residual(osb_grid *grid, double *R_dev);
  * launch the kernels directly); results are identical either way. */
 osb_status osb_rk3_step(osb_grid *grid, int nsteps);
 
+/* Forward Euler, the first-order scheme the paper offers beside RK3
+ * (Section 2.4): nsteps steps of U^{n+1} = U^n + dt R(U^n), one residual
+ * evaluation per step, on the same grid, state and precision as
+ * osb_rk3_step (the two may be mixed).  Queued on the grid's stream.
+ * Errors: NULL grid or nsteps < 0 -> OSB_ERR_INVALID_ARG; launch failure ->
+ * OSB_ERR_CUDA. */
+osb_status osb_euler_step(osb_grid *grid, int nsteps);
+
 /* Computes the diagnostics of the current state into *out (FP64 reductions,
  * deterministic order).  Synchronises the stream.  Returns
  * OSB_ERR_NONFINITE (with *out filled) if any conserved value is NaN/Inf. */

@@ -646,6 +646,32 @@ osb_status osb_rk3_step(osb_grid *g, int nsteps) {
     return OSB_OK;
 }
 
+// Forward Euler (Section 2.4 offers it beside the RK3 scheme): one stage per
+// step, U^{n+1} = U^n + dt R(U^n), written into the other accumulator
+// register; the FP32 path also writes the next step's FP32 stencil source.
+osb_status osb_euler_step(osb_grid *g, int nsteps) {
+    if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    for (int s = 0; s < nsteps; ++s) {
+        osb_status s0 = ensure_f32_copy(g);
+        if (s0 != OSB_OK) return s0;
+        StageArgs a = stage_args(g, g->cur, 0);
+        a.alpha_dt = a.beta_dt = g->prm.dt;
+        a.q_out = nullptr;
+        if (g->desc.precision == OSB_FP32) a.u32_out = g->q[1 - g->qc];
+        if (g->closure) {
+            cudaError_t e = cl::closure_correction(g->closure, a.src, a.src_is_f64, a.src_stride, &a.closure);
+            if (e != cudaSuccess) return cuda_fail(e, "closure correction");
+        }
+        cudaError_t e = g->K.stage(a);
+        if (e != cudaSuccess) return cuda_fail(e, "euler stage launch");
+        g->cur = 1 - g->cur;
+        g->qc = g->cur;
+        g->step += 1;
+        g->t = g->step * g->prm.dt;
+    }
+    return OSB_OK;
+}
+
 osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
     if (!g || !out) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
     cudaError_t e = launch_diagnostics(g->d, g->ph, g->desc.order, g->c64, g->prm.dt, g->U[g->cur], g->u_stride,

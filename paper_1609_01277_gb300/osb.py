@@ -26,6 +26,7 @@ STATUS = {0: "OSB_OK", 1: "OSB_ERR_INVALID_ARG", 2: "OSB_ERR_UNSUPPORTED", 3: "O
 # every entry point declared in include/osb.h
 EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_grid_destroy",
            "osb_init_taylor_green", "osb_set_state", "osb_get_state", "osb_set_state_device",
+           "osb_euler_step",
            "osb_get_state_device", "osb_residual", "osb_rk3_step", "osb_diagnostics",
            "osb_batch_step", "osb_batch_configure", "osb_autotune", "osb_diagnostics_noalloc",
            "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_closure_create", "osb_closure_destroy",
@@ -85,6 +86,7 @@ def load(path: str | None = None):
     L.osb_get_state_device.argtypes = [vp, vp]
     L.osb_residual.argtypes = [vp, vp]
     L.osb_rk3_step.argtypes = [vp, ctypes.c_int]
+    L.osb_euler_step.argtypes = [vp, ctypes.c_int]
     L.osb_diagnostics.argtypes = [vp, ctypes.POINTER(Diag)]
     L.osb_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
     L.osb_batch_configure.argtypes = [ctypes.c_double, ctypes.c_int]
@@ -221,6 +223,10 @@ class Grid:
 
     def step(self, nsteps: int = 1) -> None:
         check(load().osb_rk3_step(self.handle, int(nsteps)), "osb_rk3_step")
+
+    def euler_step(self, nsteps: int = 1) -> None:
+        """Forward Euler steps (Section 2.4), mixable with step()."""
+        check(load().osb_euler_step(self.handle, int(nsteps)), "osb_euler_step")
 
     def profile_start(self, max_stages: int) -> None:
         check(load().osb_profile_start(self.handle, int(max_stages)), "osb_profile_start")
