@@ -8,6 +8,7 @@ reads their FP64 diagnostics.  CLI:
 
     python -m paper_1609_01277_gb300.experiments curves --n 256 --order 4 --t-end 20
     python -m paper_1609_01277_gb300.experiments fp32-error --n 512 --order 8 --steps 200
+    python -m paper_1609_01277_gb300.experiments scalar --n 256 --order 8 --steps 20
 """
 from __future__ import annotations
 
@@ -125,6 +126,31 @@ def fp32_error(n: int, order: int, steps: int, dt: float | None = None, seed: in
     return out
 
 
+def scalar_timing(n: int, order: int, steps: int, warmup: int = 3) -> dict:
+    """Scalar advection-diffusion (Sections 3.1-3.2 equation) on an n^3 grid:
+    CUDA-event time of `steps` RK3 steps after `warmup` steps."""
+    import torch
+    from . import osb
+    osb.load()
+    g = torch.Generator(device="cpu").manual_seed(11)
+    phi = torch.randn((n, n, n), generator=g, dtype=torch.float64).cuda()
+    src = torch.randn((n, n, n), generator=g, dtype=torch.float64).cuda()
+    work = torch.empty(2 * n ** 3, dtype=torch.float64, device="cuda")
+    adv, k, dt = (1.0, -0.5, 0.25), 0.75, 1e-4
+    osb.scalar_rk3(phi, work, order, adv, k, dt, warmup, src)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    osb.scalar_rk3(phi, work, order, adv, k, dt, steps, src)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    r = order // 2
+    return dict(n=n, order=order, steps=steps, ms_per_step=ms / steps,
+                point_stages_per_s=3 * n ** 3 * steps / (ms * 1e-3),
+                fp64_tflops=(12 * r + 6) * 3 * n ** 3 * steps / (ms * 1e-3) / 1e12)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -135,6 +161,11 @@ def main(argv=None):
     c.add_argument("--every", type=int, default=50)
     c.add_argument("--precisions", default="fp64,fp32")
     c.add_argument("--curves-out", default=None, help="write the full curves as JSON here")
+    sc = sub.add_parser("scalar")
+    sc.add_argument("--n", type=int, default=256)
+    sc.add_argument("--order", type=int, default=8)
+    sc.add_argument("--steps", type=int, default=20)
+    sc.add_argument("--warmup", type=int, default=3)
     e = sub.add_parser("fp32-error")
     e.add_argument("--n", type=int, default=512)
     e.add_argument("--order", type=int, default=8)
@@ -149,6 +180,8 @@ def main(argv=None):
             with open(args.curves_out, "w") as f:
                 json.dump(runs, f)
         print(json.dumps(res))
+    elif args.cmd == "scalar":
+        print(json.dumps(scalar_timing(args.n, args.order, args.steps, args.warmup)))
     else:
         print(json.dumps(fp32_error(args.n, args.order, args.steps)))
 
