@@ -277,6 +277,11 @@ osb_status osb_closure_set_normalization(osb_closure *closure, const float *in_m
  * is added to R.  Correcting only the momentum equations (1,1,1 for rho u_i,
  * 0 for rho and rho E) plays the role of a subgrid-stress model. */
 osb_status osb_closure_set_channels(osb_closure *closure, const int *apply);
+/* on != 0: the momentum part of the correction may not feed kinetic energy at
+ * any point -- where u . C_m > 0 (u = m / rho of the state being corrected)
+ * the component of C_m along u is removed, the clipping of backscatter used
+ * by eddy-viscosity subgrid models.  Default off.  Training is unaffected. */
+osb_status osb_closure_set_dissipative(osb_closure *closure, int on);
 /* Rebuilds the BF16 tensor-core weight layouts from the FP32 parameters. */
 osb_status osb_closure_sync_weights(osb_closure *closure);
 /* C_dev (device FP32, 5*N SoA) = out_std * net(normalised Q); Q_dev device

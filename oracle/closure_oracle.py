@@ -123,9 +123,20 @@ def loss_grad(theta, Q, Cstar, mean, std, out_std, mode="bf16"):
     return loss, pack(g)
 
 
-def correction(theta, Q, mean, std, out_std, mode="bf16"):
+def correction(theta, Q, mean, std, out_std, mode="bf16", dissipative=False):
+    """C = out_std * y.  dissipative: where the momentum part feeds kinetic
+    energy (u . C_m > 0, u = m / rho) its component along u is removed."""
     y, _ = forward(theta, Q, mean, std, mode)
-    return y * np.asarray(out_std)[:, None, None, None]
+    C = y * np.asarray(out_std)[:, None, None, None]
+    if dissipative:
+        Q = np.asarray(Q, np.float64)
+        u = Q[1:4] / Q[0]
+        d = np.sum(u * C[1:4], axis=0)
+        uu = np.sum(u * u, axis=0)
+        s = np.where((d > 0) & (uu > 0), d / np.where(uu > 0, uu, 1.0), 0.0)
+        C = C.copy()
+        C[1:4] -= s * u
+    return C
 
 
 def adam(theta, m, v, g, lr, step, b1=0.9, b2=0.999, eps=1e-8):

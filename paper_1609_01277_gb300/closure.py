@@ -34,6 +34,7 @@ def _declare():
     L.osb_closure_set_normalization.argtypes = [vp, fp, fp, fp]
     L.osb_closure_sync_weights.argtypes = [vp]
     L.osb_closure_set_channels.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.osb_closure_set_dissipative.argtypes = [vp, ctypes.c_int]
     L.osb_closure_status.argtypes = [vp]
     L.osb_closure_forward.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.osb_closure_loss_grad.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp, vp]
@@ -41,7 +42,8 @@ def _declare():
     L.osb_grid_set_closure.argtypes = [vp, vp]
     L.osb_box_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     for name in ("osb_closure_create", "osb_closure_destroy", "osb_closure_set_normalization",
-                 "osb_closure_sync_weights", "osb_closure_set_channels", "osb_closure_status", "osb_closure_forward", "osb_closure_loss_grad",
+                 "osb_closure_sync_weights", "osb_closure_set_channels", "osb_closure_set_dissipative",
+                 "osb_closure_status", "osb_closure_forward", "osb_closure_loss_grad",
                  "osb_closure_adam_step", "osb_grid_set_closure", "osb_box_filter"):
         getattr(L, name).restype = ctypes.c_int
     L._closure_declared = True
@@ -122,6 +124,10 @@ class Closure:
     def set_channels(self, apply) -> None:
         arr = (ctypes.c_int * 5)(*[int(bool(v)) for v in apply])
         check(_declare().osb_closure_set_channels(self.handle, arr), "osb_closure_set_channels")
+
+    def set_dissipative(self, on: bool) -> None:
+        """Clip the momentum correction's local kinetic-energy injection."""
+        check(_declare().osb_closure_set_dissipative(self.handle, int(bool(on))), "osb_closure_set_dissipative")
 
     def forward(self, Q_dev):
         """Correction C (5, nz, ny, nx) FP32 for a device FP64 state (5, nz, ny, nx)."""
@@ -321,11 +327,16 @@ def run_experiment(n_fine=256, factor=4, t_end=10.0, snap_every=48, epochs=20, l
     ke_plain, t_plain, _ = _ke_run(g, data["X"][0], cstep, samples)
     gains = {}
     in_mean, in_std, out_std = c.norm
-    for label, apply, gain in (("momentum", (0, 1, 1, 1, 0), 1.0), ("momentum_half", (0, 1, 1, 1, 0), 0.5),
-                               ("all", (1, 1, 1, 1, 1), 1.0)):
+    for label, apply, gain, diss in (("momentum", (0, 1, 1, 1, 0), 1.0, False),
+                                     ("momentum_half", (0, 1, 1, 1, 0), 0.5, False),
+                                     ("momentum_dissipative", (0, 1, 1, 1, 0), 1.0, True),
+                                     ("momentum_half_dissipative", (0, 1, 1, 1, 0), 0.5, True),
+                                     ("all", (1, 1, 1, 1, 1), 1.0, False)):
         c.set_channels(apply)
         c.set_normalization(in_mean, in_std, out_std * gain)
+        c.set_dissipative(diss)
         gains[label] = _ke_run(g, data["X"][0], cstep, samples, closure=c)
+    c.set_dissipative(False)
     # default for later use: momentum equations only, half gain
     c.set_normalization(in_mean, in_std, out_std * 0.5)
     c.set_channels((0, 1, 1, 1, 0))

@@ -514,10 +514,32 @@ __global__ void k_sum_partials(const float *__restrict__ partial, int nparts, fl
 }
 
 // Correction added to R: C_m(p) = apply_m * out_std_m * y[p][m], in SoA (stride n).
-__global__ void k_closure_out(int n, const float *__restrict__ y, const float *__restrict__ nrm, float *__restrict__ C) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+// With the dissipative option (nrm[21] = 1) the momentum part never feeds
+// kinetic energy at a point: where u . C_m > 0 its component along u is
+// removed (C_m -= (u . C_m / |u|^2) u), the backscatter clipping of
+// eddy-viscosity subgrid models.  u = rho u_i / rho from the stencil source.
+template <typename S>
+__global__ void k_closure_out(int n, const float *__restrict__ y, const float *__restrict__ nrm, float *__restrict__ C,
+                              const S *__restrict__ Q, size_t qs) {
+    const bool dissipative = nrm[21] > 0.5f;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        float c[5];
 #pragma unroll
-        for (int c = 0; c < 5; ++c) C[(size_t)c * n + p] = nrm[16 + c] * nrm[10 + c] * y[(size_t)p * 8 + c];
+        for (int k = 0; k < 5; ++k) c[k] = nrm[16 + k] * nrm[10 + k] * y[(size_t)p * 8 + k];
+        if (dissipative) {
+            const float ri = 1.f / float(Q[p]);
+            const float u = float(Q[qs + p]) * ri, v = float(Q[2 * qs + p]) * ri, w = float(Q[3 * qs + p]) * ri;
+            const float d = u * c[1] + v * c[2] + w * c[3], uu = u * u + v * v + w * w;
+            if (d > 0.f && uu > 0.f) {
+                const float s = d / uu;
+                c[1] -= s * u;
+                c[2] -= s * v;
+                c[3] -= s * w;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) C[(size_t)k * n + p] = c[k];
+    }
 }
 
 // FP32 master parameters -> BF16 forward weights Wf[k][co][ci] (padded) and
@@ -695,7 +717,10 @@ cudaError_t closure_correction(osb_closure *c, const void *src, int src_is_f64, 
     cudaError_t e = forward_y(c, src, src_is_f64, stride);
     if (e != cudaSuccess) return e;
     const int blocks = (c->n + 255) / 256 < 1216 ? (c->n + 255) / 256 : 1216;
-    k_closure_out<<<blocks, 256, 0, c->st>>>(c->n, c->B.y, c->B.nrm, c->B.C);
+    if (src_is_f64)
+        k_closure_out<double><<<blocks, 256, 0, c->st>>>(c->n, c->B.y, c->B.nrm, c->B.C, (const double *)src, stride);
+    else
+        k_closure_out<float><<<blocks, 256, 0, c->st>>>(c->n, c->B.y, c->B.nrm, c->B.C, (const float *)src, stride);
     *C = c->B.C;
     return cudaGetLastError();
 }
@@ -792,6 +817,18 @@ osb_status osb_closure_set_channels(osb_closure *c, const int *apply) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
         set_last_error("closure: channel mask copy failed");
+        return OSB_ERR_CUDA;
+    }
+    return OSB_OK;
+}
+
+osb_status osb_closure_set_dissipative(osb_closure *c, int on) {
+    if (!c) return OSB_ERR_INVALID_ARG;
+    c->nrm_h[21] = on ? 1.f : 0.f;
+    cudaError_t e = cudaMemcpyAsync(c->B.nrm, c->nrm_h, sizeof(c->nrm_h), cudaMemcpyHostToDevice, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        set_last_error("closure: option copy failed");
         return OSB_ERR_CUDA;
     }
     return OSB_OK;

@@ -78,3 +78,30 @@ def test_adam_closed_form_first_step():
     g = np.array([0.3, -2.0, 1e-3])
     th, m, v = co.adam(np.zeros(3), np.zeros(3), np.zeros(3), g, 0.01, 1)
     assert np.allclose(th, -0.01 * np.sign(g), rtol=1e-4)
+
+
+def test_dissipative_correction_never_feeds_kinetic_energy():
+    """The clipped momentum correction satisfies u . C_m <= 0 at every point,
+    leaves points with u . C_m <= 0 untouched and only removes the component
+    along u (the perpendicular part is kept)."""
+    rng = np.random.default_rng(4)
+    shape = (8, 4, 4)
+    theta = rng.standard_normal(co.param_count()) * 0.05
+    Q = np.empty((5,) + shape)
+    Q[0] = 1.0 + 0.1 * rng.random(shape)
+    Q[1:4] = rng.standard_normal((3,) + shape)
+    Q[4] = 50.0 + rng.random(shape)
+    mean, std, out = np.zeros(5), np.ones(5), np.full(5, 0.3)
+    C0 = co.correction(theta, Q, mean, std, out, mode="exact")
+    C1 = co.correction(theta, Q, mean, std, out, mode="exact", dissipative=True)
+    u = Q[1:4] / Q[0]
+    d0, d1 = np.sum(u * C0[1:4], axis=0), np.sum(u * C1[1:4], axis=0)
+    assert np.all(d1 <= 1e-12 * np.sum(np.abs(u * C0[1:4]), axis=0))
+    keep = d0 <= 0
+    assert np.array_equal(C1[:, keep], C0[:, keep])
+    assert keep.sum() > 0 and (~keep).sum() > 0
+    # the removed part is parallel to u
+    diff = C0[1:4] - C1[1:4]
+    cross = np.cross(diff, u, axis=0)
+    assert np.max(np.abs(cross)) < 1e-12 * max(1.0, np.max(np.abs(diff)))
+    assert np.array_equal(C1[[0, 4]], C0[[0, 4]])

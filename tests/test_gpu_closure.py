@@ -57,6 +57,21 @@ def test_forward_matches_oracle(mods):
     assert _rel(Cg, Co) < 1e-2
 
 
+def test_dissipative_forward_matches_oracle(mods):
+    osb, closure, torch = mods
+    c, theta, Q, _, mean, std, out = _setup(mods)
+    c.set_dissipative(True)
+    try:
+        Cg = c.forward(torch.from_numpy(Q).cuda()).cpu().numpy()
+    finally:
+        c.set_dissipative(False)
+    Co = co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16", dissipative=True)
+    assert _rel(Cg, Co) < 1e-2
+    u = Q[1:4] / Q[0]
+    dg = np.sum(u * Cg[1:4].astype(np.float64), axis=0)
+    assert np.all(dg <= 1e-5 * np.sum(np.abs(u * Cg[1:4]), axis=0) + 1e-30)
+
+
 def test_loss_and_gradients_match_oracle(mods):
     osb, closure, torch = mods
     c, theta, Q, C, mean, std, out = _setup(mods, n=(16, 8, 12), seed=3)
