@@ -47,6 +47,7 @@ struct osb_grid {
     // ensemble stepping: this grid's device record and, when it leads a
     // batch, the batch counters and the cache of captured CUDA graphs
     BatchInst *batch_rec;
+    BatchInst *batch_rec_host;  // host staging copy of the record
     char *batch_ctl;
     std::map<std::string, cudaGraphExec_t> *graphs;
     cudaStream_t capture_st;  // library-owned stream the batch graphs are captured on
@@ -371,6 +372,7 @@ osb_status osb_grid_destroy(osb_grid *g) {
     for (int b = 0; b < 2; ++b)
         if (g->step_graph[b]) cudaGraphExecDestroy(g->step_graph[b]);
     delete[] g->ztma;
+    delete g->batch_rec_host;
     delete g;
     return OSB_OK;
 }
@@ -788,7 +790,12 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
         osb_grid *g = grids[i];
         osb_status s0 = ensure_f32_copy(g);
         if (s0 != OSB_OK) return s0;
-        static BatchInst rec;  // host staging of one record (large: holds TMA descriptors)
+        // host staging of the record (large: holds TMA descriptors), owned by the grid
+        if (!g->batch_rec_host) {
+            g->batch_rec_host = new (std::nothrow) BatchInst;
+            if (!g->batch_rec_host) return fail(OSB_ERR_INVALID_ARG, "batch: host allocation failed");
+        }
+        BatchInst &rec = *g->batch_rec_host;
         memset(&rec, 0, sizeof(rec));
         for (int par = 0; par < 2; ++par)
             for (int k = 0; k < 3; ++k) {
