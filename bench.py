@@ -474,7 +474,7 @@ def run_ours(args):
         keep = {k: v for k, v in r.items() if k != "curves"}
         best = r["closure"]["momentum_half"]
         keep["summary"] = {
-            "judge": "KE of the box-filtered 128^3 run on the 32^3 grid",
+            "reference": "KE of the box-filtered 128^3 run on the 32^3 grid",
             "ke_err_plain_32": r["plain"]["ke_err_vs_filtered_fine"],
             "ke_err_closure_32": best["ke_err_vs_filtered_fine"],
             "dissipation_err_plain_32": r["plain"]["dissipation_err"],

@@ -33,7 +33,7 @@ extern "C" {
 typedef enum {
     OSB_OK = 0,
     OSB_ERR_INVALID_ARG = 1, /* bad size, order, parameter or null pointer      */
-    OSB_ERR_UNSUPPORTED = 2, /* valid request that this build does not provide */
+    OSB_ERR_UNSUPPORTED = 2, /* valid request that the library does not provide */
     OSB_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel launch failed   */
     OSB_ERR_NONFINITE = 4,   /* the state holds NaN or Inf                      */
     OSB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
@@ -159,7 +159,7 @@ osb_status osb_euler_step(osb_grid *grid, int nsteps);
 osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
 
 /* Advances n independent grids (an ensemble of uneven sizes, Reynolds and
- * Mach numbers and time steps; spec extension of the paper's Section
+ * Mach numbers and time steps; an extension of the paper's Section
  * 3.3 solver) by nsteps RK3 steps each, in ONE persistent kernel launch that
  * is captured into a CUDA graph on first use and replayed on later calls with
  * the same grids, parities and nsteps.  Work items (step, stage phase,
@@ -248,7 +248,7 @@ osb_status osb_scalar_rk3(double *phi_dev, double *work_dev, const double *src_d
 
 /* ------------------------------------------------------------------------
  * Learned residual correction ("closure") for coarse grids.  Not in the paper
- * (its future work lists LES models, Section 1); a spec extension.
+ * (its future work lists LES models, Section 1); an extension.
  * Network: three 3x3x3 periodic convolutions 5 -> 32 -> 32 -> 5 with ReLU
  * after the first two; input: the 5 conserved fields normalised per channel
  * ((Q_c - mean_c)/std_c); output y scaled per channel by out_std_c and added

@@ -3,7 +3,7 @@
 TEST INFRASTRUCTURE, NOT PRODUCT CODE: only the tests import this module.  It
 shares nothing with the CUDA library.
 
-Network (spec learned closure, not in the paper): three 3x3x3 periodic
+Network (a learned closure; not in the paper): three 3x3x3 periodic
 cross-correlations 5 -> 32 -> 32 -> 5 with ReLU after the first two,
     z(p) = b + sum_k W[:, :, k] x(p + off_k),  off_k = (dx, dy, dz),
     k = (dz+1)*9 + (dy+1)*3 + (dx+1),

@@ -303,12 +303,12 @@ def run_experiment(n_fine=256, factor=4, t_end=10.0, snap_every=48, epochs=20, l
     data = make_training_data(n_fine, factor, samples, snap_every, order=order, Re=Re, dt_fine=dt_f)
     t_data = time.perf_counter() - t0
     times = np.array(data["t"])
-    # judge: KE of the filtered fine state (coarse-grid diagnostics)
-    judge = osb.Grid(osb.Config(n_c, n_c, n_c, order=order, Re=Re, dt=dt_f * factor))
+    # reference: KE of the filtered fine state (coarse-grid diagnostics)
+    ref_grid = osb.Grid(osb.Config(n_c, n_c, n_c, order=order, Re=Re, dt=dt_f * factor))
     ke_ref = []
     for X in data["X"]:
-        judge.set_state_device(X)
-        ke_ref.append(judge.diagnostics()["ke"])
+        ref_grid.set_state_device(X)
+        ke_ref.append(ref_grid.diagnostics()["ke"])
     ke_ref = np.array(ke_ref)
     ke_fine = np.array(data["ke_fine"])
     # training on 3 of every 4 snapshots
