@@ -465,6 +465,26 @@ def run_ours(args):
         e32["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(e32["ke_first4"], e64["ke_first4"]))
 
     if not args.no_variants and world == 1:
+        # viscous-work form B (product rule) and forward Euler, FP64 order 4
+        gB = osb.Grid(osb.Config(n, n, n, order=4, precision=osb.OSB_FP64, visc_form=osb.OSB_VISC_B, Re=w["Re"],
+                                 Mach=w["Mach"], gamma=w["gamma"], Pr=w["Pr"], dt=w["dt"]))
+        gB.init_taylor_green(noise_dev, w["noise_amp"])
+        msB, _ = time_steps(torch, gB, args.steps, args.warmup)
+        del gB
+        variants["order4_fp64_viscB"] = {"value": args.steps * 3 * npts / (msB * 1e-3), "ms_per_step": msB / args.steps}
+        gE = make_grid(osb, w, 4, "fp64", noise_dev)
+        gE.euler_step(args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(gE.stream)
+        gE.euler_step(args.steps)
+        e1.record(gE.stream)
+        torch.cuda.synchronize()
+        msE = e0.elapsed_time(e1)
+        del gE
+        variants["euler_order4_fp64"] = {"value": args.steps * npts / (msE * 1e-3), "ms_per_step": msE / args.steps,
+                                         "stages_per_step": 1}
+        torch.cuda.empty_cache()
         variants["scalar_advdiff_256^3_order8_fp64"] = run_scalar(torch, osb, n=256, order=8, steps=args.steps,
                                                                   warmup=args.warmup, peak=pk["fp64_tflops"])
 
