@@ -42,8 +42,13 @@ typedef enum {
 
 /* Arithmetic of the stencil path.  OSB_FP64: everything FP64.  OSB_FP32:
  * stencils, products and residual in FP32 with FP32 accumulation, while the
- * RK accumulator register and all diagnostics reductions stay FP64. */
-enum { OSB_FP64 = 0, OSB_FP32 = 1 };
+ * RK accumulator register and all diagnostics reductions stay FP64.
+ * OSB_DF64: stencils, products and residual in double-float arithmetic (each
+ * value the unevaluated sum of two FP32 numbers, about 48 significant bits,
+ * computed with error-free FP32 transformations), the RK accumulator and the
+ * reductions in FP64; it meets the FP64 path's accuracy bar at the FP32
+ * pipes' rate.  Learned closures and ensembles take FP64 or FP32 grids only. */
+enum { OSB_FP64 = 0, OSB_FP32 = 1, OSB_DF64 = 2 };
 
 /* Discretisation of the viscous work d_j(u_i tau_ij) in the energy equation
  * (Section 3.3, energy equation).  OSB_VISC_A differentiates the point-wise
@@ -55,7 +60,7 @@ enum { OSB_VISC_A = 0, OSB_VISC_B = 1 };
 typedef struct {
     int nx, ny, nz;  /* points per axis, each >= 1                            */
     int order;       /* central-difference order 2r: 2, 4, 6, 8, 10 or 12      */
-    int precision;   /* OSB_FP64 or OSB_FP32                                   */
+    int precision;   /* OSB_FP64, OSB_FP32 or OSB_DF64                         */
     int visc_form;   /* OSB_VISC_A or OSB_VISC_B                               */
 } osb_grid_desc;
 
@@ -131,8 +136,8 @@ osb_status osb_get_state_device(osb_grid *grid, double *dev_dst);
  * skew-symmetric convective terms (Section 3.3, skew-symmetric form),
  * pressure, viscous stress with the Laplacian by the second-derivative
  * stencil, heat flux and viscous work.  R_dev: device FP64, 5*N values,
- * caller-owned.  In OSB_FP32 grids the residual is computed in FP32 and
- * widened. */
+ * caller-owned.  In OSB_FP32 (OSB_DF64) grids the residual is computed in FP32
+ * (double-float) and widened. */
 osb_status osb_residual(osb_grid *grid, double *R_dev);
 
 /* Advances the state by nsteps steps of the low-storage third-order

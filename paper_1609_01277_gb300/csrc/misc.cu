@@ -56,6 +56,23 @@ __global__ void k_to_f32(const double *__restrict__ U, size_t us, float *__restr
         for (int m = 0; m < 5; ++m) q[m * qs + i] = d2f_bits(U[m * us + i]);
 }
 
+// Double-float copy of the accumulator; the energy field as rho E - e_ref.
+__global__ void k_to_dd(const double *__restrict__ U, size_t us, dd *__restrict__ q, size_t qs, int n, double e_ref) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) q[m * qs + i] = dd(U[m * us + i]);
+        q[4 * qs + i] = dd(U[4 * us + i] - e_ref);
+    }
+}
+
+cudaError_t launch_to_dd(const double *U, size_t u_stride, dd *q, size_t q_stride, int n, double e_ref,
+                         cudaStream_t st) {
+    int blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_to_dd<<<blocks, 256, 0, st>>>(U, u_stride, q, q_stride, n, e_ref);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_to_f32(const double *U, size_t u_stride, float *q, size_t q_stride, int n, cudaStream_t st) {
     int blocks = (n + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;

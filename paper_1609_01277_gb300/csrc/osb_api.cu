@@ -23,6 +23,7 @@ struct osb_grid {
     Phys ph;
     Coef<double> c64;
     Coef<float> c32;
+    Coef<dd> cdd;
     OrderKernels K;
     char *state;
     char *ws;
@@ -80,12 +81,12 @@ bool desc_ok(const osb_grid_desc *d) {
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return false;
     if ((long long)d->nx * d->ny * d->nz > 0x7fffffffLL) return false;
     if (d->order < 2 || d->order > 12 || (d->order & 1)) return false;
-    if (d->precision != OSB_FP64 && d->precision != OSB_FP32) return false;
+    if (d->precision != OSB_FP64 && d->precision != OSB_FP32 && d->precision != OSB_DF64) return false;
     if (d->visc_form != OSB_VISC_A && d->visc_form != OSB_VISC_B) return false;
     return true;
 }
 
-size_t tsize(const osb_grid_desc *d) { return d->precision == OSB_FP64 ? 8 : 4; }
+size_t tsize(const osb_grid_desc *d) { return d->precision == OSB_FP32 ? 4 : 8; }
 
 size_t field_bytes(size_t n, size_t es) { return round256(n * es); }
 
@@ -224,6 +225,19 @@ StageArgs base_args(const osb_grid *g) {
     a.ph = g->ph;
     a.c64 = g->c64;
     a.c32 = g->c32;
+    a.cdd = g->cdd;
+    if (g->desc.precision == OSB_DF64) {
+        const double gam = g->prm.gamma, M2 = g->prm.Mach * g->prm.Mach;
+        a.e_ref = 1.0 / (gam * (gam - 1.0) * M2);
+        const double p_ref = (gam - 1.0) * a.e_ref;
+        a.kdd.gm1 = dd(g->ph.gm1);
+        a.kdd.gM2 = dd(g->ph.gM2);
+        a.kdd.inv_re = dd(g->ph.inv_re);
+        a.kdd.kappa = dd(g->ph.kappa);
+        a.kdd.e_ref = dd(a.e_ref);
+        a.kdd.p_ref = dd(p_ref);
+        a.kdd.c_ref = dd(0.5 * a.e_ref + p_ref);
+    }
     a.precision = g->desc.precision;
     a.visc_form = g->desc.visc_form;
     a.zmarch = g->zmarch;
@@ -266,6 +280,15 @@ void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float
             c32->d2[a][k] = (float)c64->d2[a][k];
         }
     }
+}
+
+// Double-float weights: head = weight rounded to FP32, tail = the remainder.
+void make_coefs_dd(const Coef<double> &c64, Coef<dd> *cdd) {
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k <= MAXR; ++k) {
+            cdd->d1[a][k] = dd(c64.d1[a][k]);
+            cdd->d2[a][k] = dd(c64.d2[a][k]);
+        }
 }
 
 void set_last_error(const char *msg) { g_err = msg; }
@@ -319,6 +342,7 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     g->d = Dims{desc->nx, desc->ny, desc->nz, (int)n};
     g->ph = make_phys(*prm);
     make_coefs(desc->order, desc->nx, desc->ny, desc->nz, &g->c64, &g->c32);
+    make_coefs_dd(g->c64, &g->cdd);
     g->K = K;
     g->state = (char *)state_dev;
     g->ws = (char *)ws_dev;
@@ -483,6 +507,8 @@ osb_status osb_get_state_device(osb_grid *g, double *dev_dst) {
     return copy_state(g, nullptr, dev_dst, cudaMemcpyDeviceToDevice, false);
 }
 
+static osb_status ensure_f32_copy(osb_grid *g);
+
 osb_status osb_residual(osb_grid *g, double *R_dev) {
     if (!g || !R_dev) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
     if ((uintptr_t)R_dev & 7) return fail(OSB_ERR_BUFFER, "R_dev must be 8-byte aligned");
@@ -490,6 +516,14 @@ osb_status osb_residual(osb_grid *g, double *R_dev) {
     a.src = g->U[g->cur];
     a.src_is_f64 = 1;
     a.src_stride = g->u_stride;
+    if (g->desc.precision == OSB_DF64) {
+        // double-float grids read their double-float copy (energy offset by e_ref)
+        osb_status s0 = ensure_f32_copy(g);
+        if (s0 != OSB_OK) return s0;
+        a.src = g->q[g->qc];
+        a.src_is_f64 = 0;
+        a.src_stride = g->q_stride;
+    }
     a.R_out = R_dev;
     a.R_stride = g->d.n;
     if (g->closure) {
@@ -513,7 +547,9 @@ static const double RK_BETA[3] = {1.0 / 4.0, 3.0 / 20.0, 3.0 / 5.0};
 // q[qc], and the last stage writes the next copy into q[1-qc]; qc == cur.
 static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     StageArgs a = base_args(g);
-    const bool f32 = g->desc.precision == OSB_FP32;
+    // FP32 and double-float grids keep a copy of the accumulator in the stage
+    // type as the first stage's stencil source
+    const bool f32 = g->desc.precision != OSB_FP64;
     const int qc = cur;
     double *Ucur = g->U[cur], *Unext = g->U[1 - cur];
     void *src[3], *qout[3];
@@ -533,7 +569,7 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     qout[2] = nullptr;
     a.src = src[k];
     a.src_is_f64 = !f32;
-    a.src_is_u32 = f32 && k == 0;
+    a.src_is_u32 = g->desc.precision == OSB_FP32 && k == 0;
     a.src_stride = (k == 0 && !f32) ? g->u_stride : g->q_stride;
     a.U_in = (k == 0) ? Ucur : Unext;
     a.U_out = Unext;
@@ -551,8 +587,11 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
 }
 
 static osb_status ensure_f32_copy(osb_grid *g) {
-    if (g->desc.precision != OSB_FP32 || g->copy_valid) return OSB_OK;
-    cudaError_t e = launch_to_f32(g->U[g->cur], g->u_stride, (float *)g->q[g->cur], g->q_stride, g->d.n, g->st);
+    if (g->desc.precision == OSB_FP64 || g->copy_valid) return OSB_OK;
+    cudaError_t e = g->desc.precision == OSB_FP32
+                        ? launch_to_f32(g->U[g->cur], g->u_stride, (float *)g->q[g->cur], g->q_stride, g->d.n, g->st)
+                        : launch_to_dd(g->U[g->cur], g->u_stride, (dd *)g->q[g->cur], g->q_stride, g->d.n,
+                                       base_args(g).e_ref, g->st);
     if (e != cudaSuccess) return cuda_fail(e, "fp32 copy launch");
     g->copy_valid = 1;
     return OSB_OK;
@@ -659,7 +698,7 @@ osb_status osb_euler_step(osb_grid *g, int nsteps) {
         StageArgs a = stage_args(g, g->cur, 0);
         a.alpha_dt = a.beta_dt = g->prm.dt;
         a.q_out = nullptr;
-        if (g->desc.precision == OSB_FP32) a.u32_out = g->q[1 - g->qc];
+        if (g->desc.precision != OSB_FP64) a.u32_out = g->q[1 - g->qc];
         if (g->closure) {
             cudaError_t e = cl::closure_correction(g->closure, a.src, a.src_is_f64, a.src_stride, &a.closure);
             if (e != cudaSuccess) return cuda_fail(e, "closure correction");
@@ -719,7 +758,7 @@ bool g_tune_loaded = false;
 
 std::string shape_key(const osb_grid_desc &d) {
     char b[128];
-    snprintf(b, sizeof b, "%dx%dx%d/o%d/%s/v%d", d.nx, d.ny, d.nz, d.order, d.precision == OSB_FP64 ? "fp64" : "fp32",
+    snprintf(b, sizeof b, "%dx%dx%d/o%d/%s/v%d", d.nx, d.ny, d.nz, d.order, d.precision == OSB_FP64 ? "fp64" : (d.precision == OSB_FP32 ? "fp32" : "df64"),
              d.visc_form);
     return b;
 }
@@ -762,6 +801,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     for (int i = 0; i < n; ++i) {
         if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
         if (grids[i]->closure) return fail(OSB_ERR_UNSUPPORTED, "batch: grids with a learned closure step singly");
+        if (grids[i]->desc.precision == OSB_DF64) return fail(OSB_ERR_UNSUPPORTED, "ensembles take FP64 or FP32 grids");
     }
     const osb_grid *g0 = grids[0];
     for (int i = 1; i < n; ++i) {
@@ -903,6 +943,7 @@ osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) { return ba
 osb_status osb_grid_set_closure(osb_grid *g, osb_closure *c) {
     if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
     if (c && cl::closure_points(c) != g->d.n) return fail(OSB_ERR_INVALID_ARG, "closure grid size differs from the grid's");
+    if (c && g->desc.precision == OSB_DF64) return fail(OSB_ERR_UNSUPPORTED, "closures take FP64 or FP32 grids");
     g->closure = c;
     return OSB_OK;
 }

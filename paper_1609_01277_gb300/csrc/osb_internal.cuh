@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "osb.h"
+#include "dd.cuh"
 
 namespace osb {
 
@@ -67,7 +68,17 @@ struct StageArgs {
     Phys ph;
     Coef<double> c64;
     Coef<float> c32;
-    int precision;          // OSB_FP64 / OSB_FP32
+    Coef<dd> cdd;           // double-float weights (OSB_DF64)
+    // OSB_DF64: the double-float registers hold rho E - e_ref (e_ref =
+    // 1/(gamma (gamma-1) M^2), the energy of the reference state rho = T = 1 at
+    // rest), so pressure enters as p - p_ref (p_ref = (gamma-1) e_ref): the
+    // stencils annihilate constants, and the small deviations keep far more
+    // absolute accuracy than the full values.  0 in other precisions.
+    double e_ref;
+    struct {
+        dd gm1, gM2, inv_re, kappa, e_ref, p_ref, c_ref;  // c_ref = e_ref/2 + p_ref
+    } kdd;
+    int precision;          // OSB_FP64 / OSB_FP32 / OSB_DF64
     int visc_form;          // OSB_VISC_A / OSB_VISC_B
     const void *src;        // stencil source q_{k-1}
     int src_is_f64;         // 1: src holds doubles (U register), 0: type T
@@ -157,6 +168,7 @@ int closure_points(const osb_closure *c);
 // Host helpers shared by the translation units (defined in osb_api.cu).
 Phys make_phys(const osb_params &prm);
 void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float> *c32);
+void make_coefs_dd(const Coef<double> &c64, Coef<dd> *cdd);
 void set_last_error(const char *msg);
 
 // Misc kernels (init, diagnostics).
@@ -166,6 +178,8 @@ cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const C
                                double dt, const double *U, size_t stride, double *partials,
                                int max_partials, double *result, cudaStream_t st);
 int diag_num_partials(const Dims &d);
+cudaError_t launch_to_dd(const double *U, size_t u_stride, dd *q, size_t q_stride, int n, double e_ref,
+                         cudaStream_t st);
 cudaError_t launch_to_f32(const double *U, size_t u_stride, float *q, size_t q_stride, int n, cudaStream_t st);
 
 }  // namespace osb

@@ -31,6 +31,8 @@
 
 #include <string.h>
 
+#include <type_traits>
+
 #include "osb_internal.cuh"
 
 namespace osb {
@@ -45,6 +47,31 @@ template <>
 struct CoefPick<float> {
     static __device__ __forceinline__ const Coef<float> &get(const StageArgs &a) { return a.c32; }
 };
+template <>
+struct CoefPick<dd> {
+    static __device__ __forceinline__ const Coef<dd> &get(const StageArgs &a) { return a.cdd; }
+};
+template <typename T>
+constexpr bool is_dd = std::is_same<T, dd>::value;
+
+// Physical constants in the arithmetic type (double-float ones precomputed on
+// the host, so no kernel converts them).
+template <typename T>
+__device__ __forceinline__ T k_gm1(const StageArgs &a) {
+    if constexpr (is_dd<T>) return a.kdd.gm1; else return T(a.ph.gm1);
+}
+template <typename T>
+__device__ __forceinline__ T k_gM2(const StageArgs &a) {
+    if constexpr (is_dd<T>) return a.kdd.gM2; else return T(a.ph.gM2);
+}
+template <typename T>
+__device__ __forceinline__ T k_inv_re(const StageArgs &a) {
+    if constexpr (is_dd<T>) return a.kdd.inv_re; else return T(a.ph.inv_re);
+}
+template <typename T>
+__device__ __forceinline__ T k_kappa(const StageArgs &a) {
+    if constexpr (is_dd<T>) return a.kdd.kappa; else return T(a.ph.kappa);
+}
 
 __device__ __forceinline__ int wrapc(int i, int n) {
     i %= n;
@@ -81,10 +108,15 @@ enum LoadPolicy { LD_NC = 0, LD_CG = 1 };
 
 template <int POL, typename T, typename P>
 __device__ __forceinline__ T ld(const P *p) {
-    if constexpr (POL == LD_CG)
+    if constexpr (is_dd<P>) {
+        const float2 v = (POL == LD_CG) ? __ldcg(reinterpret_cast<const float2 *>(p))
+                                         : __ldg(reinterpret_cast<const float2 *>(p));
+        return dd(v.x, v.y);
+    } else if constexpr (POL == LD_CG) {
         return T(__ldcg(p));
-    else
+    } else {
         return T(__ldg(p));
+    }
 }
 
 // First derivative along AX of field f at the point (weights already / h).
@@ -107,6 +139,28 @@ __device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R> &nb, const
     return s;
 }
 
+
+// Double-float stencils: differences (sums) of the neighbours are formed with
+// exact head arithmetic and weighted into a compensated accumulator,
+// normalised once at the end (dd_acc).
+template <int R, int AX, int POL = LD_NC, typename P>
+__device__ __forceinline__ dd D1(const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &c) {
+    dd_acc s;
+#pragma unroll
+    for (int k = R; k >= 1; --k)
+        s.add_wdiff(c.d1[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+    return s.get();
+}
+template <int R, int AX, int POL = LD_NC, typename P>
+__device__ __forceinline__ dd D2(const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &c) {
+    dd_acc s;
+    const dd f0 = ld<POL, dd>(f + nb.center());
+    s.add_prod(c.d2[AX][0], f0.hi, f0.lo);
+#pragma unroll
+    for (int k = R; k >= 1; --k)
+        s.add_wsum(c.d2[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+    return s.get();
+}
 
 // Exact float -> double and round-to-nearest-even double -> float, on the
 // integer pipes (GB300 issues FP64 instructions, conversions included, at
@@ -188,8 +242,13 @@ __device__ __forceinline__ void prim_point(const StageArgs &a, int x, int y, int
     const T rinv = T(1) / rho;
     const T u = mx * rinv, v = my * rinv, w = mz * rinv;
     const T ke = T(0.5) * (mx * u + my * v + mz * w);
-    const T p = T(a.ph.gm1) * (e - ke);
-    const T temp = T(a.ph.gM2) * p * rinv;
+    // double-float: e holds rho E - e_ref, so p holds p - p_ref
+    const T p = k_gm1<T>(a) * (e - ke);
+    T temp;
+    if constexpr (is_dd<T>)
+        temp = k_gM2<T>(a) * (p + a.kdd.p_ref) * rinv;
+    else
+        temp = T(a.ph.gM2) * p * rinv;
     const T hmx = T(0.5) * mx, hmy = T(0.5) * my;
     aux[A_U * as + i] = u;
     aux[A_V * as + i] = v;
@@ -228,7 +287,7 @@ __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int
     const T gyx = D1<R, 0, POL>(V, nb, c), gyy = D1<R, 1, POL>(V, nb, c), gyz = D1<R, 2, POL>(V, nb, c);
     const T gzx = D1<R, 0, POL>(W, nb, c), gzy = D1<R, 1, POL>(W, nb, c), gzz = D1<R, 2, POL>(W, nb, c);
     const T div = gxx + gyy + gzz;
-    const T ir = T(a.ph.inv_re);
+    const T ir = k_inv_re<T>(a);
     const T tdiv = T(2.0 / 3.0) * div;
     const T txx = ir * (gxx + gxx - tdiv), tyy = ir * (gyy + gyy - tdiv), tzz = ir * (gzz + gzz - tdiv);
     const T txy = ir * (gxy + gyx), txz = ir * (gxz + gzx), tyz = ir * (gyz + gzy);
@@ -287,7 +346,11 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     for (int m = 0; m < 5; ++m) {
         const S *f = Q + m * qs;
         const T dx = D1<R, 0, POL>(f, nb, c), dy = D1<R, 1, POL>(f, nb, c), dz = D1<R, 2, POL>(f, nb, c);
-        res[m] = T(-0.5) * fma(u, dx, fma(v, dy, fma(w, dz, ld<POL, T>(f + i) * div)));
+        T qc = ld<POL, T>(f + i);
+        if constexpr (is_dd<T>) {
+            if (m == 4) qc = qc + a.kdd.e_ref;  // the full rho E multiplies div u
+        }
+        res[m] = T(-0.5) * fma(u, dx, fma(v, dy, fma(w, dz, qc * div)));
         // mass flux d_j(m_j/2): m_j is field 1+j, differentiated along j
         if (m == 1) res[0] = fma(T(-0.5), dx, res[0]);
         if (m == 2) res[0] = fma(T(-0.5), dy, res[0]);
@@ -302,8 +365,12 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     // energy flux
     res[4] -= D1<R, 0, POL>(aux + A_FX * as, nb, c) + D1<R, 1, POL>(aux + A_FY * as, nb, c) +
               D1<R, 2, POL>(aux + A_FZ * as, nb, c);
+    if constexpr (is_dd<T>) {
+        // F_j = F'_j + (e_ref/2 + p_ref) u_j with F'_j built from the deviations
+        res[4] -= a.kdd.c_ref * div;
+    }
     // viscous Laplacians: (1/Re)[sum_j L_j u_i + L_i u_i / 3]
-    const T ir = T(a.ph.inv_re), f43 = T(4.0 / 3.0);
+    const T ir = k_inv_re<T>(a), f43 = T(4.0 / 3.0);
     {
         const T *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as;
         T vx = ir * fma(f43, D2<R, 0, POL>(Uf, nb, c), D2<R, 1, POL>(Uf, nb, c) + D2<R, 2, POL>(Uf, nb, c));
@@ -321,7 +388,7 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
         res[2] += vy;
         res[3] += vz;
         const T *Tf = aux + A_T * as;
-        res[4] = fma(T(a.ph.kappa), D2<R, 0, POL>(Tf, nb, c) + D2<R, 1, POL>(Tf, nb, c) + D2<R, 2, POL>(Tf, nb, c), res[4]);
+        res[4] = fma(k_kappa<T>(a), D2<R, 0, POL>(Tf, nb, c) + D2<R, 1, POL>(Tf, nb, c) + D2<R, 2, POL>(Tf, nb, c), res[4]);
     }
 
     if (a.closure) {
@@ -331,12 +398,19 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     if (MODE == 0) {
         T *qo = static_cast<T *>(a.q_out);
         if constexpr (sizeof(T) == 8) {
+            // FP64 and double-float: the accumulator update in FP64; the
+            // double-float path also writes the next step's double-float
+            // copy of the accumulator in the last stage
+            T *cp = static_cast<T *>(a.u32_out);
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
                 const double Ui = ld<POL, double>(a.U_in + m * a.u_stride + i);
                 const double Rm = double(res[m]);
-                a.U_out[m * a.u_stride + i] = fma(a.beta_dt, Rm, Ui);
-                if (qo) qo[m * a.q_stride + i] = T(fma(a.alpha_dt, Rm, Ui));
+                const double Un = fma(a.beta_dt, Rm, Ui);
+                a.U_out[m * a.u_stride + i] = Un;
+                const double off = (is_dd<T> && m == 4) ? a.e_ref : 0.0;  // double-float registers: rho E - e_ref
+                if (qo) qo[m * a.q_stride + i] = T(fma(a.alpha_dt, Rm, Ui) - off);
+                if (cp) cp[m * a.q_stride + i] = T(Un - off);
             }
         } else {
             // FP32 path: the FP64 accumulator takes one DADD per field; the
@@ -391,6 +465,8 @@ cudaError_t launch_stage_form(const StageArgs &a, int mode) {
 template <int R>
 cudaError_t launch_stage(const StageArgs &a, int mode) {
     if (a.precision == OSB_FP64) return launch_stage_form<double, double, R>(a, mode);
+    if (a.precision == OSB_DF64)
+        return a.src_is_f64 ? launch_stage_form<double, dd, R>(a, mode) : launch_stage_form<dd, dd, R>(a, mode);
     if (a.src_is_f64) return launch_stage_form<double, float, R>(a, mode);
     return launch_stage_form<float, float, R>(a, mode);
 }

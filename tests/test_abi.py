@@ -62,6 +62,8 @@ def test_sizes(osb):
     assert L.osb_state_bytes(ctypes.byref(d)) == 20 * n * 8
     d32 = osb.GridDesc(32, 32, 32, 4, osb.OSB_FP32, 0)
     assert L.osb_state_bytes(ctypes.byref(d32)) == 10 * n * 8 + 10 * n * 4
+    ddd = osb.GridDesc(32, 32, 32, 4, osb.OSB_DF64, 0)   # double-float registers: 8 bytes per value
+    assert L.osb_state_bytes(ctypes.byref(ddd)) == 20 * n * 8
     assert L.osb_workspace_bytes(ctypes.byref(d)) > 15 * n * 8
     bad = osb.GridDesc(32, 32, 32, 5, osb.OSB_FP64, 0)
     assert L.osb_state_bytes(ctypes.byref(bad)) == 0
@@ -70,7 +72,7 @@ def test_sizes(osb):
 
 @pytest.mark.parametrize("desc", [
     (0, 8, 8, 4, 0, 0), (8, 8, 8, 3, 0, 0), (8, 8, 8, 14, 0, 0), (8, 8, 8, 0, 0, 0),
-    (8, 8, 8, 4, 2, 0), (8, 8, 8, 4, 0, 7), (2048, 2048, 1024, 4, 0, 0)])
+    (8, 8, 8, 4, 3, 0), (8, 8, 8, 4, 0, 7), (2048, 2048, 1024, 4, 0, 0)])
 def test_invalid_descriptor_rejected(osb, desc):
     st, h = _create(osb, osb.GridDesc(*desc), osb.Params(1600, 0.1, 1.4, 0.71, 1e-3), sb=1 << 40, wb=1 << 40)
     assert st == 1 and not h.value
