@@ -229,7 +229,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def make_grid(osb, w, order, precision, noise):
     cfg = osb.Config(w["n"], w["n"], w["n"], order=order,
-                     precision=osb.OSB_FP64 if precision == "fp64" else osb.OSB_FP32,
+                     precision={"fp64": osb.OSB_FP64, "fp32": osb.OSB_FP32, "df64": osb.OSB_DF64}[precision],
                      Re=w["Re"], Mach=w["Mach"], gamma=w["gamma"], Pr=w["Pr"], dt=w["dt"])
     g = osb.Grid(cfg)
     g.init_taylor_green(noise, w["noise_amp"])
@@ -456,6 +456,21 @@ def run_ours(args):
             variants[f"order{order}_fp32"]["ke_err_vs_fp64"] = err
             variants[f"order{order}_fp32"]["speedup_vs_fp64"] = (
                 variants[f"order{order}_fp32"]["value"] / variants[f"order{order}_fp64"]["value"])
+        # double-float arithmetic (FP64-class accuracy on the FP32 pipes)
+        for order in (4, 8):
+            gd = make_grid(osb, w, order, "df64", noise_dev)
+            dms, dprof = time_steps(torch, gd, args.steps, args.warmup, profile=True)
+            del gd
+            gk = make_grid(osb, w, order, "df64", noise_dev)
+            series = ke_series(torch, gk, min(args.steps, 10))
+            del gk
+            b = ref_ke[order]["fp64"]
+            variants[f"order{order}_df64"] = {
+                "value": args.steps * 3 * npts / (dms * 1e-3), "ms_per_step": dms / args.steps,
+                "kernel_avg_ms": {k: v["total_ms"] / max(v["launches"], 1) for k, v in dprof.items()},
+                "ke_err_vs_fp64": max(abs(x - y) for x, y in zip(series, b)) / b[0],
+                "speedup_vs_fp64": args.steps * 3 * npts / (dms * 1e-3) / variants[f"order{order}_fp64"]["value"]}
+            torch.cuda.empty_cache()
 
     if not args.no_ensemble and world == 1:
         for prec in ("fp64", "fp32"):
