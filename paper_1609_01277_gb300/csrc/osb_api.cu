@@ -237,6 +237,14 @@ StageArgs base_args(const osb_grid *g) {
         a.kdd.e_ref = dd(a.e_ref);
         a.kdd.p_ref = dd(p_ref);
         a.kdd.c_ref = dd(0.5 * a.e_ref + p_ref);
+        for (int ax = 0; ax < 3; ++ax)
+            for (int k = 0; k <= MAXR; ++k) {
+                const double d2 = g->c64.d2[ax][k], d1 = g->c64.d1[ax][k], ir = g->ph.inv_re;
+                a.cdd_vis.d2[ax][k] = dd(ir * d2);
+                a.cdd_vis43.d2[ax][k] = dd(ir * (4.0 / 3.0) * d2);
+                a.cdd_heat.d2[ax][k] = dd(g->ph.kappa * d2);
+                a.cdd_g.d1[ax][k] = dd(ir * (1.0 / 3.0) * d1);
+            }
     }
     a.precision = g->desc.precision;
     a.visc_form = g->desc.visc_form;

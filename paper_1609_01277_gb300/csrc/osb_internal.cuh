@@ -78,6 +78,10 @@ struct StageArgs {
     struct {
         dd gm1, gM2, inv_re, kappa, e_ref, p_ref, c_ref;  // c_ref = e_ref/2 + p_ref
     } kdd;
+    // OSB_DF64 residual: second-derivative weights scaled by 1/Re, 4/(3 Re) and
+    // kappa, first-derivative weights by 1/(3 Re), so each equation's terms
+    // accumulate without separate multiplications
+    Coef<dd> cdd_vis, cdd_vis43, cdd_heat, cdd_g;
     int precision;          // OSB_FP64 / OSB_FP32 / OSB_DF64
     int visc_form;          // OSB_VISC_A / OSB_VISC_B
     const void *src;        // stencil source q_{k-1}

@@ -324,6 +324,121 @@ __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// Double-float residual: every term of an equation goes into one compensated
+// accumulator (dd_acc) -- the flux divergences, Laplacians and heat flux with
+// their constant factors folded into the stencil weights, the advective
+// products as products -- normalised once per equation.
+// ---------------------------------------------------------------------------
+template <int R, int AX, int POL, typename P>
+__device__ __forceinline__ void acc_d1(dd_acc &acc, const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &w,
+                                       bool negate) {
+#pragma unroll
+    for (int k = R; k >= 1; --k) {
+        const dd wk = negate ? -w.d1[AX][k] : w.d1[AX][k];
+        acc.add_wdiff(wk, ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+    }
+}
+template <int R, int AX, int POL, typename P>
+__device__ __forceinline__ void acc_d2(dd_acc &acc, const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &w,
+                                       const dd &f0) {
+    acc.add_prod(w.d2[AX][0], f0.hi, f0.lo);
+#pragma unroll
+    for (int k = R; k >= 1; --k)
+        acc.add_wsum(w.d2[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+}
+__device__ __forceinline__ dd dd_scale(const dd &x, float s) { return dd(x.hi * s, x.lo * s); }  // s a power of 2
+
+template <int POL, typename S, int R, bool VB>
+__device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> &nb, int i, dd (&res)[5]) {
+    const Coef<dd> &c = a.cdd;
+    const S *Q = static_cast<const S *>(a.src);
+    const size_t qs = a.src_stride;
+    const dd *aux = static_cast<const dd *>(a.aux);
+    const size_t as = a.aux_stride;
+    const dd u = ld<POL, dd>(aux + A_U * as + i), v = ld<POL, dd>(aux + A_V * as + i);
+    const dd w = ld<POL, dd>(aux + A_W * as + i), div = ld<POL, dd>(aux + A_DIV * as + i);
+    const dd hu = dd_scale(u, -0.5f), hv = dd_scale(v, -0.5f), hw = dd_scale(w, -0.5f), hdiv = dd_scale(div, -0.5f);
+    dd_acc acc[5];
+    // advective + dilatation half of the skew-symmetric form; mass flux
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const S *f = Q + m * qs;
+        const dd dx = D1<R, 0, POL>(f, nb, c), dy = D1<R, 1, POL>(f, nb, c), dz = D1<R, 2, POL>(f, nb, c);
+        acc[m].add_prod(hu, dx.hi, dx.lo);
+        acc[m].add_prod(hv, dy.hi, dy.lo);
+        acc[m].add_prod(hw, dz.hi, dz.lo);
+        dd qc = ld<POL, dd>(f + i);
+        if (m == 4) qc = qc + a.kdd.e_ref;  // the full rho E multiplies div u
+        acc[m].add_prod(hdiv, qc.hi, qc.lo);
+        if (m == 1) acc[0].add_prod(dd(-0.5f, 0.f), dx.hi, dx.lo);
+        if (m == 2) acc[0].add_prod(dd(-0.5f, 0.f), dy.hi, dy.lo);
+        if (m == 3) acc[0].add_prod(dd(-0.5f, 0.f), dz.hi, dz.lo);
+    }
+    // momentum fluxes -D_j Phi_ij and energy flux -D_j F'_j - c_ref div u
+    const dd *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
+    const dd *Pxy = aux + A_PXY * as, *Pxz = aux + A_PXZ * as, *Pyz = aux + A_PYZ * as;
+    acc_d1<R, 0, POL>(acc[1], Pxx, nb, c, true);
+    acc_d1<R, 1, POL>(acc[1], Pxy, nb, c, true);
+    acc_d1<R, 2, POL>(acc[1], Pxz, nb, c, true);
+    acc_d1<R, 0, POL>(acc[2], Pxy, nb, c, true);
+    acc_d1<R, 1, POL>(acc[2], Pyy, nb, c, true);
+    acc_d1<R, 2, POL>(acc[2], Pyz, nb, c, true);
+    acc_d1<R, 0, POL>(acc[3], Pxz, nb, c, true);
+    acc_d1<R, 1, POL>(acc[3], Pyz, nb, c, true);
+    acc_d1<R, 2, POL>(acc[3], Pzz, nb, c, true);
+    acc_d1<R, 0, POL>(acc[4], aux + A_FX * as, nb, c, true);
+    acc_d1<R, 1, POL>(acc[4], aux + A_FY * as, nb, c, true);
+    acc_d1<R, 2, POL>(acc[4], aux + A_FZ * as, nb, c, true);
+    acc[4].add_prod(-a.kdd.c_ref, div.hi, div.lo);
+    // viscous Laplacians (1/Re)[sum_j L_j u_i + L_i u_i / 3]
+    const dd *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as;
+    if (!VB) {
+        acc_d2<R, 0, POL>(acc[1], Uf, nb, a.cdd_vis43, u);
+        acc_d2<R, 1, POL>(acc[1], Uf, nb, a.cdd_vis, u);
+        acc_d2<R, 2, POL>(acc[1], Uf, nb, a.cdd_vis, u);
+        acc_d2<R, 0, POL>(acc[2], Vf, nb, a.cdd_vis, v);
+        acc_d2<R, 1, POL>(acc[2], Vf, nb, a.cdd_vis43, v);
+        acc_d2<R, 2, POL>(acc[2], Vf, nb, a.cdd_vis, v);
+        acc_d2<R, 0, POL>(acc[3], Wf, nb, a.cdd_vis, w);
+        acc_d2<R, 1, POL>(acc[3], Wf, nb, a.cdd_vis, w);
+        acc_d2<R, 2, POL>(acc[3], Wf, nb, a.cdd_vis43, w);
+    } else {
+        // form B: the viscous momentum term (with D_i g_i / 3) is also needed
+        // as a value for the work u_i (viscous term) + tau : grad u
+        dd_acc vx, vy, vz;
+        acc_d2<R, 0, POL>(vx, Uf, nb, a.cdd_vis43, u);
+        acc_d2<R, 1, POL>(vx, Uf, nb, a.cdd_vis, u);
+        acc_d2<R, 2, POL>(vx, Uf, nb, a.cdd_vis, u);
+        acc_d1<R, 0, POL>(vx, aux + A_GX * as, nb, a.cdd_g, false);
+        acc_d2<R, 0, POL>(vy, Vf, nb, a.cdd_vis, v);
+        acc_d2<R, 1, POL>(vy, Vf, nb, a.cdd_vis43, v);
+        acc_d2<R, 2, POL>(vy, Vf, nb, a.cdd_vis, v);
+        acc_d1<R, 1, POL>(vy, aux + A_GY * as, nb, a.cdd_g, false);
+        acc_d2<R, 0, POL>(vz, Wf, nb, a.cdd_vis, w);
+        acc_d2<R, 1, POL>(vz, Wf, nb, a.cdd_vis, w);
+        acc_d2<R, 2, POL>(vz, Wf, nb, a.cdd_vis43, w);
+        acc_d1<R, 2, POL>(vz, aux + A_GZ * as, nb, a.cdd_g, false);
+        const dd VX = vx.get(), VY = vy.get(), VZ = vz.get();
+        acc[1].add_prod(dd(1.f, 0.f), VX.hi, VX.lo);
+        acc[2].add_prod(dd(1.f, 0.f), VY.hi, VY.lo);
+        acc[3].add_prod(dd(1.f, 0.f), VZ.hi, VZ.lo);
+        acc[4].add_prod(u, VX.hi, VX.lo);
+        acc[4].add_prod(v, VY.hi, VY.lo);
+        acc[4].add_prod(w, VZ.hi, VZ.lo);
+        const dd tg = ld<POL, dd>(aux + A_TG * as + i);
+        acc[4].add_prod(dd(1.f, 0.f), tg.hi, tg.lo);
+    }
+    // heat flux kappa sum_j L_j T
+    const dd *Tf = aux + A_T * as;
+    const dd T0 = ld<POL, dd>(Tf + i);
+    acc_d2<R, 0, POL>(acc[4], Tf, nb, a.cdd_heat, T0);
+    acc_d2<R, 1, POL>(acc[4], Tf, nb, a.cdd_heat, T0);
+    acc_d2<R, 2, POL>(acc[4], Tf, nb, a.cdd_heat, T0);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) res[m] = acc[m].get();
+}
+
+// ---------------------------------------------------------------------------
 // k_resid: residual and RK update (MODE 0) or residual only (MODE 1)
 // ---------------------------------------------------------------------------
 template <int POL, typename S, typename T, int R, int MODE, bool VB>
@@ -337,10 +452,13 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     const T *aux = static_cast<const T *>(a.aux);
     const size_t as = a.aux_stride;
 
+    T res[5];
+    if constexpr (is_dd<T>) {
+        resid_terms_dd<POL, S, R, VB>(a, nb, i, res);
+    } else {
     const T u = ld<POL, T>(aux + A_U * as + i), v = ld<POL, T>(aux + A_V * as + i);
     const T w = ld<POL, T>(aux + A_W * as + i), div = ld<POL, T>(aux + A_DIV * as + i);
 
-    T res[5];
     // advective + dilatation half of the skew-symmetric form, per field
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
@@ -389,6 +507,7 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
         res[3] += vz;
         const T *Tf = aux + A_T * as;
         res[4] = fma(k_kappa<T>(a), D2<R, 0, POL>(Tf, nb, c) + D2<R, 1, POL>(Tf, nb, c) + D2<R, 2, POL>(Tf, nb, c), res[4]);
+    }
     }
 
     if (a.closure) {

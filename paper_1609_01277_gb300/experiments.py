@@ -9,6 +9,7 @@ reads their FP64 diagnostics.  CLI:
     python -m paper_1609_01277_gb300.experiments curves --n 256 --order 4 --t-end 20
     python -m paper_1609_01277_gb300.experiments fp32-error --n 512 --order 8 --steps 200
     python -m paper_1609_01277_gb300.experiments scalar --n 256 --order 8 --steps 20
+    python -m paper_1609_01277_gb300.experiments steps --n 256 --order 4 --precision df64
 """
 from __future__ import annotations
 
@@ -151,6 +152,30 @@ def scalar_timing(n: int, order: int, steps: int, warmup: int = 3) -> dict:
                 fp64_tflops=(12 * r + 6) * 3 * n ** 3 * steps / (ms * 1e-3) / 1e12)
 
 
+def step_timing(n: int, order: int, precision: str, steps: int, warmup: int = 3) -> dict:
+    """Taylor-Green steps on an n^3 grid in the given precision (fp64, fp32,
+    df64): CUDA-event time per step and per kernel kind."""
+    import torch
+    from . import inputs, osb
+    osb.load()
+    prec = {"fp64": osb.OSB_FP64, "fp32": osb.OSB_FP32, "df64": osb.OSB_DF64}[precision]
+    g = osb.Grid(osb.Config(n, n, n, order=order, precision=prec, dt=default_dt(n)))
+    g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1234)).cuda(), 1e-4)
+    g.step(warmup)
+    torch.cuda.synchronize()
+    g.profile_start(3 * steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.step(steps)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    prof = g.profile_stop()
+    ms = e0.elapsed_time(e1)
+    return dict(n=n, order=order, precision=precision, steps=steps, ms_per_step=ms / steps,
+                point_stages_per_s=3 * n ** 3 * steps / (ms * 1e-3),
+                kernel_ms={k: v["total_ms"] / max(v["launches"], 1) for k, v in prof.items()})
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -166,6 +191,12 @@ def main(argv=None):
     sc.add_argument("--order", type=int, default=8)
     sc.add_argument("--steps", type=int, default=20)
     sc.add_argument("--warmup", type=int, default=3)
+    st = sub.add_parser("steps")
+    st.add_argument("--n", type=int, default=256)
+    st.add_argument("--order", type=int, default=4)
+    st.add_argument("--precision", default="df64", choices=("fp64", "fp32", "df64"))
+    st.add_argument("--steps", type=int, default=10)
+    st.add_argument("--warmup", type=int, default=3)
     e = sub.add_parser("fp32-error")
     e.add_argument("--n", type=int, default=512)
     e.add_argument("--order", type=int, default=8)
@@ -180,6 +211,8 @@ def main(argv=None):
             with open(args.curves_out, "w") as f:
                 json.dump(runs, f)
         print(json.dumps(res))
+    elif args.cmd == "steps":
+        print(json.dumps(step_timing(args.n, args.order, args.precision, args.steps, args.warmup)))
     elif args.cmd == "scalar":
         print(json.dumps(scalar_timing(args.n, args.order, args.steps, args.warmup)))
     else:
