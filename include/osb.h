@@ -47,7 +47,7 @@ typedef enum {
  * value the unevaluated sum of two FP32 numbers, about 48 significant bits,
  * computed with error-free FP32 transformations), the RK accumulator and the
  * reductions in FP64; it meets the FP64 path's accuracy bar at the FP32
- * pipes' rate.  Learned closures and ensembles take FP64 or FP32 grids only. */
+ * pipes' rate.  Learned closures take FP64 or FP32 grids only. */
 enum { OSB_FP64 = 0, OSB_FP32 = 1, OSB_DF64 = 2 };
 
 /* Discretisation of the viscous work d_j(u_i tau_ij) in the energy equation

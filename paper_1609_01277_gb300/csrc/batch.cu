@@ -228,6 +228,8 @@ static cudaError_t launch_batch_r(const BatchParams &P, int precision, int visc_
     }
     if (precision == OSB_FP64)
         return visc_form == OSB_VISC_B ? launch_batch_t<double, R, true>(P, st) : launch_batch_t<double, R, false>(P, st);
+    if (precision == OSB_DF64)
+        return visc_form == OSB_VISC_B ? launch_batch_t<dd, R, true>(P, st) : launch_batch_t<dd, R, false>(P, st);
     return visc_form == OSB_VISC_B ? launch_batch_t<float, R, true>(P, st) : launch_batch_t<float, R, false>(P, st);
 }
 

@@ -26,18 +26,43 @@
 
 namespace osb {
 
+// Rounded FP32 operations that the compiler may not fuse into FMAs: the
+// error-free transformations below rely on every sum and product being
+// rounded on its own.
+__host__ __device__ __forceinline__ float fadd_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fadd_rn(a, b);
+#else
+    return a + b;
+#endif
+}
+__host__ __device__ __forceinline__ float fsub_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fsub_rn(a, b);
+#else
+    return a - b;
+#endif
+}
+__host__ __device__ __forceinline__ float fmul_rn(float a, float b) {
+#ifdef __CUDA_ARCH__
+    return __fmul_rn(a, b);
+#else
+    return a * b;
+#endif
+}
+
 __host__ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float ap = s - b;
-    const float bp = s - ap;
-    e = (a - ap) + (b - bp);
+    s = fadd_rn(a, b);
+    const float ap = fsub_rn(s, b);
+    const float bp = fsub_rn(s, ap);
+    e = fadd_rn(fsub_rn(a, ap), fsub_rn(b, bp));
 }
 __host__ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    e = b - (s - a);
+    s = fadd_rn(a, b);
+    e = fsub_rn(b, fsub_rn(s, a));
 }
 __host__ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-    p = a * b;
+    p = fmul_rn(a, b);
     e = fmaf(a, b, -p);
 }
 
@@ -157,9 +182,9 @@ __host__ __device__ __forceinline__ dd operator+(const dd &x, const dd &y) {
     float sh, sl, th, tl, vh, vl;
     two_sum(x.hi, y.hi, sh, sl);
     two_sum(x.lo, y.lo, th, tl);
-    const float c = sl + th;
+    const float c = fadd_rn(sl, th);
     fast_two_sum(sh, c, vh, vl);
-    const float w = tl + vl;
+    const float w = fadd_rn(tl, vl);
     return dd_norm(vh, w);
 }
 __host__ __device__ __forceinline__ dd operator-(const dd &x) { return dd(-x.hi, -x.lo); }
@@ -169,10 +194,10 @@ __host__ __device__ __forceinline__ dd operator-(const dd &x, const dd &y) { ret
 __host__ __device__ __forceinline__ dd operator*(const dd &x, const dd &y) {
     float ch, cl1;
     two_prod(x.hi, y.hi, ch, cl1);
-    const float tl0 = x.lo * y.lo;
+    const float tl0 = fmul_rn(x.lo, y.lo);
     const float tl1 = fmaf(x.hi, y.lo, tl0);
     const float cl2 = fmaf(x.lo, y.hi, tl1);
-    return dd_norm(ch, cl1 + cl2);
+    return dd_norm(ch, fadd_rn(cl1, cl2));
 }
 
 __host__ __device__ __forceinline__ dd fma(const dd &a, const dd &b, const dd &c) { return a * b + c; }
@@ -204,14 +229,14 @@ struct dd_acc {
     __host__ __device__ __forceinline__ void add_wdiff(const dd &w, const dd &a, const dd &b) {
         float dh, d1;
         two_sum(a.hi, -b.hi, dh, d1);
-        const float dl = d1 + (a.lo - b.lo);
+        const float dl = fadd_rn(d1, fsub_rn(a.lo, b.lo));
         add_prod(w, dh, dl);
     }
     // add w * (a + b)
     __host__ __device__ __forceinline__ void add_wsum(const dd &w, const dd &a, const dd &b) {
         float dh, d1;
         two_sum(a.hi, b.hi, dh, d1);
-        const float dl = d1 + (a.lo + b.lo);
+        const float dl = fadd_rn(d1, fadd_rn(a.lo, b.lo));
         add_prod(w, dh, dl);
     }
     // add w * (dh + dl)
@@ -223,7 +248,7 @@ struct dd_acc {
         const float s0 = s;
         float t;
         two_sum(s0, p, s, t);
-        e += t + pe;
+        e = fadd_rn(e, fadd_rn(t, pe));
     }
     __host__ __device__ __forceinline__ dd get() const { return dd_norm(s, e); }
 };

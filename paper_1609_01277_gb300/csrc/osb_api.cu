@@ -809,7 +809,6 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     for (int i = 0; i < n; ++i) {
         if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
         if (grids[i]->closure) return fail(OSB_ERR_UNSUPPORTED, "batch: grids with a learned closure step singly");
-        if (grids[i]->desc.precision == OSB_DF64) return fail(OSB_ERR_UNSUPPORTED, "ensembles take FP64 or FP32 grids");
     }
     const osb_grid *g0 = grids[0];
     for (int i = 1; i < n; ++i) {

@@ -346,7 +346,7 @@ __device__ __forceinline__ void acc_d2(dd_acc &acc, const P *__restrict__ f, con
     for (int k = R; k >= 1; --k)
         acc.add_wsum(w.d2[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
 }
-__device__ __forceinline__ dd dd_scale(const dd &x, float s) { return dd(x.hi * s, x.lo * s); }  // s a power of 2
+__device__ __forceinline__ dd dd_scale(const dd &x, float s) { return dd(__fmul_rn(x.hi, s), __fmul_rn(x.lo, s)); }  // s a power of 2
 
 template <int POL, typename S, int R, bool VB>
 __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> &nb, int i, dd (&res)[5]) {

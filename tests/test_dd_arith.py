@@ -20,7 +20,8 @@ def test_double_float_arithmetic_error_bounds(tmp_path):
     if nvcc is None:
         pytest.skip("nvcc not available")
     exe = str(tmp_path / "dd_check")
-    subprocess.run([nvcc, "-O2", "-std=c++17", "-o", exe, os.path.join(ROOT, "tests", "dd_check.cu"),
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-Xcompiler", "-ffp-contract=off", "-o", exe,
+                    os.path.join(ROOT, "tests", "dd_check.cu"),
                     "-I", os.path.join(ROOT, "paper_1609_01277_gb300", "csrc")],
                    check=True, capture_output=True, timeout=300)
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)

@@ -127,8 +127,21 @@ def test_df64_graph_replay_equals_direct_launches(osb, monkeypatch):
     assert np.array_equal(a.get_state(), b.get_state())
 
 
-def test_df64_rejects_ensembles_and_closures(osb):
-    g = _grid(osb, 8, 8, 8, order=4)
-    with pytest.raises(osb.OsbError) as ei:
-        osb.batch_step([g], 1)
-    assert ei.value.status == 2
+def test_df64_ensemble_equals_per_grid_steps(osb):
+    """The persistent ensemble kernel runs the same double-float stage code."""
+    specs = [(16, 800.0, 2e-3), (20, 1600.0, 1e-3), (12, 300.0, 3e-3)]
+    a, b = [], []
+    for i, (n, Re, dt) in enumerate(specs):
+        for lst in (a, b):
+            g = _grid(osb, n, n, n, order=4, Re=Re, dt=dt)
+            g.init_taylor_green(inputs.gaussian_noise(n, n, n, 60 + i), 1e-3)
+            lst.append(g)
+    osb.batch_step(b, 3)
+    for ga, gb, (n, Re, dt), i in zip(a, b, specs, range(3)):
+        ga.step(3)
+        A, B = ga.get_state(), gb.get_state()
+        assert np.max(np.abs(A - B)) <= 1e-13 * np.max(np.abs(A))
+        case = _case(n, n, n, order=4, Re=Re, dt=dt)
+        Qo = orc.rk3_step(case, orc.tgv_init(case, inputs.gaussian_noise(n, n, n, 60 + i), 1e-3), 3)
+        for m, err in rel_l2_fields(B, Qo).items():
+            assert err < TOL, (m, err)
