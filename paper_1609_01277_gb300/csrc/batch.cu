@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(BX *BY) k_batch(const BatchParams P) {
             const unsigned target = P.inject_stall ? 0xffffffffu : (unsigned)(seq * tiles_i);
             if (ld_acquire_u32(P.done + inst) < target) {
                 const unsigned long long t0 = globaltimer();
+                unsigned nap = 32;  // exponential backoff: many CTAs poll one counter
                 while (true) {
                     if (ld_volatile_i32(P.err)) {
                         stop_s = 1;
@@ -72,7 +73,8 @@ __global__ void __launch_bounds__(BX *BY) k_batch(const BatchParams P) {
                         stop_s = 1;
                         break;
                     }
-                    __nanosleep(256);
+                    __nanosleep(nap);
+                    nap = nap < 2048 ? 2 * nap : 2048;
                 }
             }
         }
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(zm::NT, (R <= 2) ? 2 : 1) k_batch_z(const Batc
             const unsigned target = P.inject_stall ? 0xffffffffu : (unsigned)(seq * tiles_i);
             if (ld_acquire_u32(P.done + inst) < target) {
                 const unsigned long long t0 = globaltimer();
+                unsigned nap = 32;  // exponential backoff: many CTAs poll one counter
                 while (true) {
                     if (ld_volatile_i32(P.err)) {
                         stop_s = 1;
@@ -157,7 +160,8 @@ __global__ void __launch_bounds__(zm::NT, (R <= 2) ? 2 : 1) k_batch_z(const Batc
                         stop_s = 1;
                         break;
                     }
-                    __nanosleep(256);
+                    __nanosleep(nap);
+                    nap = nap < 2048 ? 2 * nap : 2048;
                 }
             }
         }

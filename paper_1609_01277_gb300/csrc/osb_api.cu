@@ -515,7 +515,7 @@ osb_status osb_get_state_device(osb_grid *g, double *dev_dst) {
     return copy_state(g, nullptr, dev_dst, cudaMemcpyDeviceToDevice, false);
 }
 
-static osb_status ensure_f32_copy(osb_grid *g);
+static osb_status ensure_stage_copy(osb_grid *g);
 
 osb_status osb_residual(osb_grid *g, double *R_dev) {
     if (!g || !R_dev) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
@@ -526,7 +526,7 @@ osb_status osb_residual(osb_grid *g, double *R_dev) {
     a.src_stride = g->u_stride;
     if (g->desc.precision == OSB_DF64) {
         // double-float grids read their double-float copy (energy offset by e_ref)
-        osb_status s0 = ensure_f32_copy(g);
+        osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;
         a.src = g->q[g->qc];
         a.src_is_f64 = 0;
@@ -594,19 +594,19 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     return a;
 }
 
-static osb_status ensure_f32_copy(osb_grid *g) {
+static osb_status ensure_stage_copy(osb_grid *g) {
     if (g->desc.precision == OSB_FP64 || g->copy_valid) return OSB_OK;
     cudaError_t e = g->desc.precision == OSB_FP32
                         ? launch_to_f32(g->U[g->cur], g->u_stride, (float *)g->q[g->cur], g->q_stride, g->d.n, g->st)
                         : launch_to_dd(g->U[g->cur], g->u_stride, (dd *)g->q[g->cur], g->q_stride, g->d.n,
                                        base_args(g).e_ref, g->st);
-    if (e != cudaSuccess) return cuda_fail(e, "fp32 copy launch");
+    if (e != cudaSuccess) return cuda_fail(e, "stage-type copy launch");
     g->copy_valid = 1;
     return OSB_OK;
 }
 
 static osb_status rk3_one_step(osb_grid *g) {
-    osb_status s0 = ensure_f32_copy(g);
+    osb_status s0 = ensure_stage_copy(g);
     if (s0 != OSB_OK) return s0;
     for (int k = 0; k < 3; ++k) {
         StageArgs a = stage_args(g, g->cur, k);
@@ -673,7 +673,7 @@ osb_status osb_rk3_step(osb_grid *g, int nsteps) {
     const char *env = getenv("OSB_GRAPHS");
     const bool graphs = nsteps >= 2 && !g->closure && !g->prof_ev && !(env && strcmp(env, "0") == 0);
     if (graphs) {
-        osb_status s0 = ensure_f32_copy(g);
+        osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;
         for (int s = 0; s < nsteps; ++s) {
             cudaGraphExec_t ge = nullptr;
@@ -701,7 +701,7 @@ osb_status osb_rk3_step(osb_grid *g, int nsteps) {
 osb_status osb_euler_step(osb_grid *g, int nsteps) {
     if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
     for (int s = 0; s < nsteps; ++s) {
-        osb_status s0 = ensure_f32_copy(g);
+        osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;
         StageArgs a = stage_args(g, g->cur, 0);
         a.alpha_dt = a.beta_dt = g->prm.dt;
@@ -835,7 +835,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
                       std::to_string((long long)(g_batch_cfg.wait_limit_s * 1e9));
     for (int i = 0; i < n; ++i) {
         osb_grid *g = grids[i];
-        osb_status s0 = ensure_f32_copy(g);
+        osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;
         // host staging of the record (large: holds TMA descriptors), owned by the grid
         if (!g->batch_rec_host) {
