@@ -287,6 +287,10 @@ osb_status osb_closure_set_channels(osb_closure *closure, const int *apply);
  * the component of C_m along u is removed, the clipping of backscatter used
  * by eddy-viscosity subgrid models.  Default off.  Training is unaffected. */
 osb_status osb_closure_set_dissipative(osb_closure *closure, int on);
+/* Weight w > 0 multiplying the loss and every gradient of the following
+ * osb_closure_loss_grad calls (default 1): per-sample weighting of the
+ * training loss. */
+osb_status osb_closure_set_loss_weight(osb_closure *closure, float w);
 /* Rebuilds the BF16 tensor-core weight layouts from the FP32 parameters. */
 osb_status osb_closure_sync_weights(osb_closure *closure);
 /* C_dev (device FP32, 5*N SoA) = out_std * net(normalised Q); Q_dev device

@@ -35,6 +35,7 @@ def _declare():
     L.osb_closure_sync_weights.argtypes = [vp]
     L.osb_closure_set_channels.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.osb_closure_set_dissipative.argtypes = [vp, ctypes.c_int]
+    L.osb_closure_set_loss_weight.argtypes = [vp, ctypes.c_float]
     L.osb_closure_status.argtypes = [vp]
     L.osb_closure_forward.argtypes = [vp, vp, ctypes.c_size_t, vp]
     L.osb_closure_loss_grad.argtypes = [vp, vp, ctypes.c_size_t, vp, ctypes.c_size_t, vp, vp]
@@ -43,6 +44,7 @@ def _declare():
     L.osb_box_filter.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp]
     for name in ("osb_closure_create", "osb_closure_destroy", "osb_closure_set_normalization",
                  "osb_closure_sync_weights", "osb_closure_set_channels", "osb_closure_set_dissipative",
+                 "osb_closure_set_loss_weight",
                  "osb_closure_status", "osb_closure_forward", "osb_closure_loss_grad",
                  "osb_closure_adam_step", "osb_grid_set_closure", "osb_box_filter"):
         getattr(L, name).restype = ctypes.c_int
@@ -124,6 +126,9 @@ class Closure:
     def set_channels(self, apply) -> None:
         arr = (ctypes.c_int * 5)(*[int(bool(v)) for v in apply])
         check(_declare().osb_closure_set_channels(self.handle, arr), "osb_closure_set_channels")
+
+    def set_loss_weight(self, w: float) -> None:
+        check(_declare().osb_closure_set_loss_weight(self.handle, float(w)), "osb_closure_set_loss_weight")
 
     def set_dissipative(self, on: bool) -> None:
         """Clip the momentum correction's local kinetic-energy injection."""
@@ -217,16 +222,31 @@ def normalisation(data):
     return in_mean, in_std, out_std
 
 
-def train(closure: Closure, data, epochs: int, lr: float = 1e-3, train_idx=None, seed: int = 0):
+def train(closure: Closure, data, epochs: int, lr: float = 1e-3, train_idx=None, seed: int = 0,
+          relative: bool = False):
+    """Adam over the snapshots in random order.  relative: weight each
+    snapshot's loss by the inverse mean square of its normalised target (mean
+    weight 1), so snapshots with a small commutation residual -- the smooth
+    early flow -- are fitted in relative terms too."""
     rng = np.random.Generator(np.random.PCG64(seed))
     idx = list(range(len(data["X"]))) if train_idx is None else list(train_idx)
+    weights = {i: 1.0 for i in idx}
+    if relative:
+        import torch
+        out_std = torch.tensor(np.asarray(closure.norm[2], dtype=np.float64), device=data["Y"][0].device).view(5, 1, 1, 1)
+        ms = {i: float(((data["Y"][i] / out_std) ** 2).mean()) for i in idx}
+        inv = {i: 1.0 / max(ms[i], 1e-30) for i in idx}
+        mean_inv = float(np.mean(list(inv.values())))
+        weights = {i: inv[i] / mean_inv for i in idx}
     hist = []
     for _ in range(epochs):
         order = rng.permutation(idx)
         tot = 0.0
         for i in order:
+            closure.set_loss_weight(weights[int(i)])
             tot += float(closure.train_step(data["X"][i], data["Y"][i], lr).item())
         hist.append(tot / len(order))
+    closure.set_loss_weight(1.0)
     return hist
 
 
@@ -289,7 +309,7 @@ def _ke_run(grid, X0, steps_per_sample, samples, closure=None, history=4):
 
 
 def run_experiment(n_fine=256, factor=4, t_end=10.0, snap_every=48, epochs=20, lr=1e-3, Re=1600.0, order=4,
-                   seed=0):
+                   seed=0, relative=False):
     """Fine run -> filtered training data -> training -> a-posteriori KE-decay
     comparison of the coarse grid with and without the closure (and the plain
     solver at twice the coarse resolution), against the filtered fine run."""
@@ -317,7 +337,7 @@ def run_experiment(n_fine=256, factor=4, t_end=10.0, snap_every=48, epochs=20, l
     c = Closure(n_c, n_c, n_c, seed=seed)
     c.set_normalization(*normalisation(data))
     t0 = time.perf_counter()
-    hist = train(c, data, epochs, lr=lr, train_idx=train_idx, seed=seed)
+    hist = train(c, data, epochs, lr=lr, train_idx=train_idx, seed=seed, relative=relative)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     apriori = dict(plain=a_priori_error(None, data, test_idx), closure=a_priori_error(c, data, test_idx))
@@ -389,11 +409,12 @@ if __name__ == "__main__":
     ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--relative", action="store_true", help="weight each snapshot by its inverse mean-square target")
     a = ap.parse_args()
     from . import build
     build.build()
     osb.load()
-    r = run_experiment(a.fine, a.factor, a.t_end, a.snap_every, a.epochs, a.lr)
+    r = run_experiment(a.fine, a.factor, a.t_end, a.snap_every, a.epochs, a.lr, relative=a.relative)
     if a.out:
         with open(a.out, "w") as f:
             json.dump(r, f)

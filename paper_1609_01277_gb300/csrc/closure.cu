@@ -478,8 +478,8 @@ __global__ void k_targets(int n, const double *__restrict__ C, size_t cs, const 
 
 // MSE on the normalised output: loss partials and dy = 2 (y - t) / (5 N) (BF16, 16 channels).
 __global__ void __launch_bounds__(256) k_mse(int n, const float *__restrict__ y, const float *__restrict__ t,
-                                             uint16_t *__restrict__ dy, float *__restrict__ partial) {
-    const float sc = 2.f / (5.f * n);
+                                             uint16_t *__restrict__ dy, float *__restrict__ partial, float weight) {
+    const float sc = 2.f * weight / (5.f * n);
     double s = 0.0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
         uint32_t w[8];
@@ -691,6 +691,7 @@ struct osb_closure {
     osb::cl::Buffers B;
     cudaStream_t st;
     float nrm_h[24];
+    float loss_weight;  // multiplies the loss and its gradient (per-sample weighting)
 };
 
 namespace osb {
@@ -770,6 +771,7 @@ osb_status osb_closure_create(int nx, int ny, int nz, float *params_dev, void *w
     c->st = (cudaStream_t)stream;
     cl::carve(c->ws, c->n, &c->B);
     for (int i = 0; i < 24; ++i) c->nrm_h[i] = ((i >= 5 && i < 15) || (i >= 16 && i < 21)) ? 1.f : 0.f;
+    c->loss_weight = 1.f;
     // zero the padded BF16 weight buffers once (padding entries stay zero)
     cudaError_t e = cudaMemsetAsync(c->B.tcerr, 0, (char *)c->ws + need - (char *)c->B.tcerr, c->st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->B.nrm, c->nrm_h, sizeof(c->nrm_h), cudaMemcpyHostToDevice, c->st);
@@ -819,6 +821,12 @@ osb_status osb_closure_set_channels(osb_closure *c, const int *apply) {
         set_last_error("closure: channel mask copy failed");
         return OSB_ERR_CUDA;
     }
+    return OSB_OK;
+}
+
+osb_status osb_closure_set_loss_weight(osb_closure *c, float w) {
+    if (!c || !(w > 0) || !isfinite(w)) return OSB_ERR_INVALID_ARG;
+    c->loss_weight = w;
     return OSB_OK;
 }
 
@@ -872,8 +880,8 @@ osb_status osb_closure_loss_grad(osb_closure *c, const double *X_dev, size_t xs,
     const int blocks = (n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216;
     if (e == cudaSuccess) {
         k_targets<<<blocks, 256, 0, c->st>>>(n, Cstar_dev, cs, c->B.nrm, c->B.t);
-        k_mse<<<NPART, 256, 0, c->st>>>(n, c->B.y, c->B.t, c->B.dy, c->B.lpart);
-        k_sum_partials<<<1, 32, 0, c->st>>>(c->B.lpart, NPART, 1.f / (5.f * n), loss_dev);
+        k_mse<<<NPART, 256, 0, c->st>>>(n, c->B.y, c->B.t, c->B.dy, c->B.lpart, c->loss_weight);
+        k_sum_partials<<<1, 32, 0, c->st>>>(c->B.lpart, NPART, c->loss_weight / (5.f * n), loss_dev);
         e = cudaGetLastError();
     }
     // layer 3: dW3, db3; then dz2 = (W3^T dy) * [h2 > 0]

@@ -30,7 +30,7 @@ EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_gri
            "osb_get_state_device", "osb_residual", "osb_rk3_step", "osb_diagnostics",
            "osb_batch_step", "osb_batch_configure", "osb_autotune", "osb_diagnostics_noalloc",
            "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_closure_create", "osb_closure_destroy",
-           "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_set_dissipative", "osb_closure_status", "osb_closure_sync_weights",
+           "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_set_dissipative", "osb_closure_set_loss_weight", "osb_closure_status", "osb_closure_sync_weights",
            "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
            "osb_box_filter", "osb_scalar_rk3", "osb_profile_start", "osb_profile_stop",
            "osb_status_string", "osb_last_error")

@@ -84,6 +84,22 @@ def test_loss_and_gradients_match_oracle(mods):
         assert _rel(P[name], Po[name]) < 2e-2, name
 
 
+def test_loss_weight_scales_loss_and_gradient(mods):
+    osb, closure, torch = mods
+    c, theta, Q, C, *_ = _setup(mods, n=(16, 8, 12), seed=3)
+    Qd, Cd = torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda()
+    l1, g1 = c.loss_grad(Qd, Cd)       # the closure's own output buffers: copy before the next call
+    l1 = float(l1.item())
+    g1 = g1.cpu().numpy().astype(np.float64)
+    c.set_loss_weight(4.0)   # a power of two: the BF16 output gradient scales exactly
+    try:
+        l4, g4 = c.loss_grad(Qd, Cd)
+    finally:
+        c.set_loss_weight(1.0)
+    assert float(l4.item()) == pytest.approx(4.0 * l1, rel=1e-6)
+    assert _rel(g4.cpu().numpy().astype(np.float64), 4.0 * g1) < 1e-5
+
+
 def test_adam_step_matches_formula(mods):
     osb, closure, torch = mods
     c, theta, Q, C, *_ = _setup(mods, seed=5)
