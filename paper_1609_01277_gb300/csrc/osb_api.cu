@@ -889,6 +889,13 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     osb_grid *lead = grids[0];
     if (!lead->graphs) lead->graphs = new std::map<std::string, cudaGraphExec_t>();
     cudaGraphExec_t exec = nullptr;
+    // the captured launch bakes in every field of P (record addresses, tile
+    // prefix sums, parities, counters): key the cache on all of it, so a grid
+    // destroyed and re-created at the same host address never replays a stale
+    // graph
+    key.append(reinterpret_cast<const char *>(&P), sizeof(P));
+    key += "|" + std::to_string(g0->desc.order) + ":" + std::to_string(g0->desc.precision) + ":" +
+           std::to_string(g0->desc.visc_form) + ":" + std::to_string((int)zmode);
     auto it = lead->graphs->find(key);
     if (it != lead->graphs->end()) {
         exec = it->second;
