@@ -217,6 +217,9 @@ __host__ __device__ __forceinline__ dd operator/(const dd &x, const dd &y) {
     return q + dd(r2.hi / y.hi, 0.f);
 }
 
+// exact scaling by a power of two s
+__host__ __device__ __forceinline__ dd dd_scale(const dd &x, float s) { return dd(fmul_rn(x.hi, s), fmul_rn(x.lo, s)); }
+
 __host__ __device__ __forceinline__ dd &operator+=(dd &a, const dd &b) { return a = a + b; }
 __host__ __device__ __forceinline__ dd &operator-=(dd &a, const dd &b) { return a = a - b; }
 

@@ -273,8 +273,15 @@ __global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
 // ---------------------------------------------------------------------------
 // k_grad: velocity gradient -> div u, tau_ij, energy flux, viscous g-term
 // ---------------------------------------------------------------------------
+template <int POL, typename S, int R>
+__device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z);
+
 template <int POL, typename S, typename T, int R, bool VB>
 __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int z) {
+    if constexpr (is_dd<T> && !VB) {
+        grad_point_dd<POL, S, R>(a, x, y, z);
+        return;
+    } else {
     Nbr<R> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
@@ -314,6 +321,83 @@ __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int
         aux[A_TG * as + i] = txx * gxx + tyy * gyy + tzz * gzz + txy * (gxy + gyx) + txz * (gxz + gzx) +
                              tyz * (gyz + gzy);
     }
+    }
+}
+
+// Double-float gradient kernel (viscous form A): the energy flux
+// F_j = hE u_j - u_i tau_ij is expanded into products of a velocity with one
+// gradient entry, tau_ij = (1/Re)(g_ij + g_ji - (2/3) div u delta_ij), and
+// accumulated compensated; likewise Phi_ii - (1/(3Re)) sum_{k != i} g_kk.
+__device__ __forceinline__ void acc_add(dd_acc &acc, const dd &w, const dd &x) { acc.add_prod(w, x.hi, x.lo); }
+
+template <int POL, typename S, int R>
+__device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z) {
+    Nbr<R> nb;
+    nb.init(x, y, z, a.d);
+    const int i = nb.center();
+    const Coef<dd> &c = a.cdd;
+    dd *aux = static_cast<dd *>(a.aux);
+    const size_t as = a.aux_stride;
+    const dd *U = aux + A_U * as, *V = aux + A_V * as, *W = aux + A_W * as;
+    const dd gxx = D1<R, 0, POL>(U, nb, c), gxy = D1<R, 1, POL>(U, nb, c), gxz = D1<R, 2, POL>(U, nb, c);
+    const dd gyx = D1<R, 0, POL>(V, nb, c), gyy = D1<R, 1, POL>(V, nb, c), gyz = D1<R, 2, POL>(V, nb, c);
+    const dd gzx = D1<R, 0, POL>(W, nb, c), gzy = D1<R, 1, POL>(W, nb, c), gzz = D1<R, 2, POL>(W, nb, c);
+    dd_acc dv;
+    const dd one(1.f, 0.f);
+    acc_add(dv, one, gxx);
+    acc_add(dv, one, gyy);
+    acc_add(dv, one, gzz);
+    const dd div = dv.get();
+    const dd u = ld<POL, dd>(aux + A_U * as + i), v = ld<POL, dd>(aux + A_V * as + i);
+    const dd w = ld<POL, dd>(aux + A_W * as + i), p = ld<POL, dd>(aux + A_P * as + i);
+    const S *Q = static_cast<const S *>(a.src);
+    const dd hE = dd_scale(ld<POL, dd>(Q + 4 * a.src_stride + i), 0.5f) + p;
+    aux[A_DIV * as + i] = div;
+    const dd ir = a.kdd.inv_re;
+    const dd iru = ir * u, irv = ir * v, irw = ir * w;
+    const dd m2u = dd_scale(iru, -2.f), m2v = dd_scale(irv, -2.f), m2w = dd_scale(irw, -2.f);
+    const dd two3 = dd(2.0 / 3.0);
+    const dd tdiv = two3 * div;  // (2/3) div u
+    const dd niru = -iru, nirv = -irv, nirw = -irw;
+    dd_acc fx, fy, fz;
+    acc_add(fx, hE, u);
+    acc_add(fx, m2u, gxx);
+    acc_add(fx, iru, tdiv);
+    acc_add(fx, nirv, gxy);
+    acc_add(fx, nirv, gyx);
+    acc_add(fx, nirw, gxz);
+    acc_add(fx, nirw, gzx);
+    acc_add(fy, hE, v);
+    acc_add(fy, niru, gxy);
+    acc_add(fy, niru, gyx);
+    acc_add(fy, m2v, gyy);
+    acc_add(fy, irv, tdiv);
+    acc_add(fy, nirw, gyz);
+    acc_add(fy, nirw, gzy);
+    acc_add(fz, hE, w);
+    acc_add(fz, niru, gxz);
+    acc_add(fz, niru, gzx);
+    acc_add(fz, nirv, gyz);
+    acc_add(fz, nirv, gzy);
+    acc_add(fz, m2w, gzz);
+    acc_add(fz, irw, tdiv);
+    aux[A_FX * as + i] = fx.get();
+    aux[A_FY * as + i] = fy.get();
+    aux[A_FZ * as + i] = fz.get();
+    const dd nir3 = -(ir * dd(1.0 / 3.0));
+    dd_acc px, py, pz;
+    acc_add(px, one, ld<POL, dd>(aux + A_PXX * as + i));
+    acc_add(px, nir3, gyy);
+    acc_add(px, nir3, gzz);
+    acc_add(py, one, ld<POL, dd>(aux + A_PYY * as + i));
+    acc_add(py, nir3, gxx);
+    acc_add(py, nir3, gzz);
+    acc_add(pz, one, ld<POL, dd>(aux + A_PZZ * as + i));
+    acc_add(pz, nir3, gxx);
+    acc_add(pz, nir3, gyy);
+    aux[A_PXX * as + i] = px.get();
+    aux[A_PYY * as + i] = py.get();
+    aux[A_PZZ * as + i] = pz.get();
 }
 
 template <typename S, typename T, int R, bool VB>
@@ -346,7 +430,6 @@ __device__ __forceinline__ void acc_d2(dd_acc &acc, const P *__restrict__ f, con
     for (int k = R; k >= 1; --k)
         acc.add_wsum(w.d2[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
 }
-__device__ __forceinline__ dd dd_scale(const dd &x, float s) { return dd(__fmul_rn(x.hi, s), __fmul_rn(x.lo, s)); }  // s a power of 2
 
 template <int POL, typename S, int R, bool VB>
 __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> &nb, int i, dd (&res)[5]) {
