@@ -642,6 +642,17 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     resid_point<LD_NC, S, T, R, MODE, VB>(a, x, y, z);
 }
 
+// Double-float residual kernel with explicit occupancy targets: three CTAs per
+// SM up to order 4 (a few spilled registers buy 24 resident warps to hide the
+// neighbour-load latency this kernel waits on), two for orders 6 and 8, one
+// (all registers, no spills) for orders 10 and 12.
+template <typename S, int R, int MODE, bool VB>
+__global__ void __launch_bounds__(BX *BY, R <= 2 ? 3 : (R <= 4 ? 2 : 1)) k_resid_dd(const StageArgs a) {
+    const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
+    if (x >= a.d.nx || y >= a.d.ny) return;
+    resid_point<LD_NC, S, dd, R, MODE, VB>(a, x, y, z);
+}
+
 template <typename S, typename T, int R, bool VB>
 cudaError_t launch_stage_typed(const StageArgs &a, int mode) {
     dim3 blk(BX, BY, 1), grd((a.d.nx + BX - 1) / BX, (a.d.ny + BY - 1) / BY, a.d.nz);
@@ -650,10 +661,17 @@ cudaError_t launch_stage_typed(const StageArgs &a, int mode) {
     if (a.ev) cudaEventRecord(a.ev[1], a.stream);
     k_grad<S, T, R, VB><<<grd, blk, 0, a.stream>>>(a);
     if (a.ev) cudaEventRecord(a.ev[2], a.stream);
-    if (mode == 0)
-        k_resid<S, T, R, 0, VB><<<grd, blk, 0, a.stream>>>(a);
-    else
-        k_resid<S, T, R, 1, VB><<<grd, blk, 0, a.stream>>>(a);
+    if constexpr (is_dd<T>) {
+        if (mode == 0)
+            k_resid_dd<S, R, 0, VB><<<grd, blk, 0, a.stream>>>(a);
+        else
+            k_resid_dd<S, R, 1, VB><<<grd, blk, 0, a.stream>>>(a);
+    } else {
+        if (mode == 0)
+            k_resid<S, T, R, 0, VB><<<grd, blk, 0, a.stream>>>(a);
+        else
+            k_resid<S, T, R, 1, VB><<<grd, blk, 0, a.stream>>>(a);
+    }
     if (a.ev) cudaEventRecord(a.ev[3], a.stream);
     return cudaGetLastError();
 }
