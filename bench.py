@@ -272,7 +272,7 @@ def ensemble_specs(count=64, seed=7):
 
 def run_ensemble(torch, osb, inputs, steps, precision):
     specs = ensemble_specs()
-    prec = osb.OSB_FP64 if precision == "fp64" else osb.OSB_FP32
+    prec = {"fp64": osb.OSB_FP64, "fp32": osb.OSB_FP32, "df64": osb.OSB_DF64}[precision]
     grids = []
     for i, e in enumerate(specs):
         n = e["n"]
@@ -305,8 +305,8 @@ def run_ensemble(torch, osb, inputs, steps, precision):
             "value": steps * 3 * pts / t_batch, "ms_per_step": 1e3 * t_batch / steps,
             "per_grid_launch_value": steps * 3 * pts / t_seq, "speedup_vs_per_grid_launches": t_seq / t_batch,
             "ke_first4": ke, "launches_per_step": 1,
-            "per_grid_launches_per_step": (9 if precision == "fp64" else 6) * len(specs),
-            "items": "three-kernel point items" if precision == "fp64" else "z-march column items"}
+            "per_grid_launches_per_step": (6 if precision == "fp32" else 9) * len(specs),
+            "items": "z-march column items" if precision == "fp32" else "three-kernel point items"}
 
 
 def run_scalar(torch, osb, n, order, steps, warmup, peak):
@@ -473,11 +473,14 @@ def run_ours(args):
             torch.cuda.empty_cache()
 
     if not args.no_ensemble and world == 1:
-        for prec in ("fp64", "fp32"):
+        for prec in ("fp64", "fp32", "df64"):
             variants[f"ensemble64_order4_{prec}"] = run_ensemble(torch, osb, inputs, args.ensemble_steps, prec)
         e64, e32 = variants["ensemble64_order4_fp64"], variants["ensemble64_order4_fp32"]
         e32["speedup_vs_fp64_ensemble"] = e32["value"] / e64["value"]
         e32["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(e32["ke_first4"], e64["ke_first4"]))
+        edd = variants["ensemble64_order4_df64"]
+        edd["speedup_vs_fp64_ensemble"] = edd["value"] / e64["value"]
+        edd["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(edd["ke_first4"], e64["ke_first4"]))
 
     if not args.no_variants and world == 1:
         # viscous-work form B (product rule) and forward Euler, FP64 order 4

@@ -36,7 +36,20 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 }
 
 template <typename T, int R, bool VB>
+__device__ __forceinline__ void batch_loop(const BatchParams &P);
+
+template <typename T, int R, bool VB>
 __global__ void __launch_bounds__(BX *BY) k_batch(const BatchParams P) {
+    batch_loop<T, R, VB>(P);
+}
+// double-float items: bounded to two CTAs per SM (128 registers)
+template <int R, bool VB>
+__global__ void __launch_bounds__(BX *BY, 2) k_batch_dd(const BatchParams P) {
+    batch_loop<dd, R, VB>(P);
+}
+
+template <typename T, int R, bool VB>
+__device__ __forceinline__ void batch_loop(const BatchParams &P) {
     __shared__ StageArgs sa;
     __shared__ long long item_s;
     __shared__ int stop_s;
@@ -216,12 +229,18 @@ static cudaError_t launch_batch_t(const BatchParams &P, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<T, R, VB>, BX * BY, 0);
+    if constexpr (is_dd<T>)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_dd<R, VB>, BX * BY, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<T, R, VB>, BX * BY, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)per_sm * sms;
     if (blocks > P.total_items) blocks = P.total_items > 0 ? P.total_items : 1;
-    k_batch<T, R, VB><<<(unsigned)blocks, dim3(BX, BY, 1), 0, st>>>(P);
+    if constexpr (is_dd<T>)
+        k_batch_dd<R, VB><<<(unsigned)blocks, dim3(BX, BY, 1), 0, st>>>(P);
+    else
+        k_batch<T, R, VB><<<(unsigned)blocks, dim3(BX, BY, 1), 0, st>>>(P);
     return cudaGetLastError();
 }
 
