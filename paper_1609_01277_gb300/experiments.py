@@ -10,6 +10,7 @@ reads their FP64 diagnostics.  CLI:
     python -m paper_1609_01277_gb300.experiments fp32-error --n 512 --order 8 --steps 200
     python -m paper_1609_01277_gb300.experiments scalar --n 256 --order 8 --steps 20
     python -m paper_1609_01277_gb300.experiments steps --n 256 --order 4 --precision df64
+    python -m paper_1609_01277_gb300.experiments closure --n 64
 """
 from __future__ import annotations
 
@@ -176,6 +177,40 @@ def step_timing(n: int, order: int, precision: str, steps: int, warmup: int = 3)
                 kernel_ms={k: v["total_ms"] / max(v["launches"], 1) for k, v in prof.items()})
 
 
+def closure_timing(n: int, reps: int, warmup: int = 2) -> dict:
+    """Learned-closure network on an n^3 grid: CUDA-event time of one forward
+    pass and of one loss + gradient evaluation (BF16 tensor-core convolutions),
+    with the forward pass's dense flop count (2 x 27 taps x channel products
+    per point: 5->32, 32->32, 32->5)."""
+    import torch
+    from . import closure as clo, inputs, osb
+    osb.load()
+    c = clo.Closure(n, n, n, seed=0)
+    g = osb.Grid(osb.Config(n, n, n, order=4))
+    g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 3)).cuda(), 1e-3)
+    Q = g.get_state_device()
+    c.set_normalization(Q.mean(dim=(1, 2, 3)).cpu().numpy(), Q.std(dim=(1, 2, 3)).cpu().numpy() + 1e-6,
+                        np.ones(5))
+    Cstar = torch.zeros_like(Q)
+    for _ in range(warmup):
+        c.forward(Q)
+        c.loss_grad(Q, Cstar)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(reps):
+        c.forward(Q)
+    e[1].record()
+    for _ in range(reps):
+        c.loss_grad(Q, Cstar)
+    e[2].record()
+    torch.cuda.synchronize()
+    fwd_ms, bwd_ms = e[0].elapsed_time(e[1]) / reps, e[1].elapsed_time(e[2]) / reps
+    flops = 2 * 27 * (5 * 32 + 32 * 32 + 32 * 5) * n ** 3
+    return dict(n=n, forward_ms=fwd_ms, loss_grad_ms=bwd_ms, forward_gflop=flops / 1e9,
+                forward_tflops=flops / (fwd_ms * 1e-3) / 1e12)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -197,6 +232,9 @@ def main(argv=None):
     st.add_argument("--precision", default="df64", choices=("fp64", "fp32", "df64"))
     st.add_argument("--steps", type=int, default=10)
     st.add_argument("--warmup", type=int, default=3)
+    cl = sub.add_parser("closure")
+    cl.add_argument("--n", type=int, default=64)
+    cl.add_argument("--reps", type=int, default=10)
     e = sub.add_parser("fp32-error")
     e.add_argument("--n", type=int, default=512)
     e.add_argument("--order", type=int, default=8)
@@ -213,6 +251,8 @@ def main(argv=None):
         print(json.dumps(res))
     elif args.cmd == "steps":
         print(json.dumps(step_timing(args.n, args.order, args.precision, args.steps, args.warmup)))
+    elif args.cmd == "closure":
+        print(json.dumps(closure_timing(args.n, args.reps)))
     elif args.cmd == "scalar":
         print(json.dumps(scalar_timing(args.n, args.order, args.steps, args.warmup)))
     else:
