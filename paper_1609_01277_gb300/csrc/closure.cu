@@ -180,6 +180,12 @@ constexpr size_t tc_smem_used() {
     return (size_t)THN * CI * 2 + (size_t)27 * CI * CO * 2;
 }
 
+// 16-byte global -> shared copy that skips the registers (and L1).
+__device__ __forceinline__ void tc_cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+
 template <int CI, int CO, int EPI>
 __global__ void __launch_bounds__(128) k_conv_tc(int nx, int ny, int nz, const uint16_t *__restrict__ in,
                                                  const uint16_t *__restrict__ W, const float *__restrict__ bias,
@@ -213,16 +219,17 @@ __global__ void __launch_bounds__(128) k_conv_tc(int nx, int ny, int nz, const u
         const int hx = pos % THX, hy = (pos / THX) % THY, hz = pos / (THX * THY);
         const int gx = wrapi(x0 + hx - 1, nx), gy = wrapi(y0 + hy - 1, ny), gz = wrapi(z0 + hz - 1, nz);
         const size_t gp = ((size_t)gz * ny + gy) * nx + gx;
-        *reinterpret_cast<uint4 *>(A + ((size_t)ch * THN + pos) * 16) =
-            *reinterpret_cast<const uint4 *>(in + gp * CI + ch * 8);
+        tc_cp_async16(A + ((size_t)ch * THN + pos) * 16, in + gp * CI + ch * 8);
     }
     // weights [27][CO][CI] -> B [27][NCH][CO][8]
     for (int e = tid; e < 27 * CO * NCH; e += 128) {
         const int k = e / (CO * NCH), n = (e / NCH) % CO, ch = e % NCH;
-        *reinterpret_cast<uint4 *>(B + (((size_t)k * NCH + ch) * CO + n) * 16) =
-            *reinterpret_cast<const uint4 *>(W + ((size_t)k * CO + n) * CI + ch * 8);
+        tc_cp_async16(B + (((size_t)k * NCH + ch) * CO + n) * 16, W + ((size_t)k * CO + n) * CI + ch * 8);
     }
-    // make the generic-proxy shared-memory writes visible to the tensor cores
+    // all of this thread's copies in flight at once, then one wait
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    // make the shared-memory writes visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
