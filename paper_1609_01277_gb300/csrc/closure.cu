@@ -48,6 +48,16 @@ __device__ __forceinline__ float bf16_val(uint16_t b) { return __bfloat162float(
 // ---------------------------------------------------------------------------
 enum { EPI_RELU = 0, EPI_LIN = 1, EPI_MASK = 2 };
 
+// 16-byte global -> shared copy that skips the registers (and L1).
+__device__ __forceinline__ void tc_cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 template <int CI, int CO, int EPI>
 __global__ void __launch_bounds__(256) k_conv(int nx, int ny, int nz, const uint16_t *__restrict__ in,
                                               const uint16_t *__restrict__ W, const float *__restrict__ bias,
@@ -69,12 +79,13 @@ __global__ void __launch_bounds__(256) k_conv(int nx, int ny, int nz, const uint
         const int hx = hp % HX, hy = (hp / HX) % HY, hz = hp / (HX * HY);
         const int gx = wrapi(x0 + hx - 1, nx), gy = wrapi(y0 + hy - 1, ny), gz = wrapi(z0 + hz - 1, nz);
         const size_t gp = ((size_t)gz * ny + gy) * nx + gx;
-        *reinterpret_cast<uint4 *>(in_s + hp * SI + ch * 8) = *reinterpret_cast<const uint4 *>(in + gp * CI + ch * 8);
+        tc_cp_async16(in_s + hp * SI + ch * 8, in + gp * CI + ch * 8);
     }
     for (int e = tid; e < 27 * CO * CH; e += 256) {
         const int row = e / CH, ch = e - row * CH;  // row = k*CO + co
-        *reinterpret_cast<uint4 *>(w_s + row * SW + ch * 8) = *reinterpret_cast<const uint4 *>(W + row * CI + ch * 8);
+        tc_cp_async16(w_s + row * SW + ch * 8, W + row * CI + ch * 8);
     }
+    cp_async_wait_all();
     __syncthreads();
 
     const int g = lane >> 2, tg = lane & 3;
@@ -180,12 +191,6 @@ constexpr size_t tc_smem_used() {
     return (size_t)THN * CI * 2 + (size_t)27 * CI * CO * 2;
 }
 
-// 16-byte global -> shared copy that skips the registers (and L1).
-__device__ __forceinline__ void tc_cp_async16(void *smem, const void *gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-
 template <int CI, int CO, int EPI>
 __global__ void __launch_bounds__(128) k_conv_tc(int nx, int ny, int nz, const uint16_t *__restrict__ in,
                                                  const uint16_t *__restrict__ W, const float *__restrict__ bias,
@@ -227,8 +232,7 @@ __global__ void __launch_bounds__(128) k_conv_tc(int nx, int ny, int nz, const u
         tc_cp_async16(B + (((size_t)k * NCH + ch) * CO + n) * 16, W + ((size_t)k * CO + n) * CI + ch * 8);
     }
     // all of this thread's copies in flight at once, then one wait
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    cp_async_wait_all();
     // make the shared-memory writes visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -359,15 +363,16 @@ __global__ void __launch_bounds__(256) k_wgrad(int nx, int ny, int nz, const uin
             const int p = e / (CO / 8), ch = e - p * (CO / 8);
             const int gx = x0 + p % PX, gy = y0 + (p / PX) % PY, gz = z0 + p / (PX * PY);
             const size_t gp = ((size_t)gz * ny + gy) * nx + gx;
-            *reinterpret_cast<uint4 *>(dz_s + p * SD + ch * 8) = *reinterpret_cast<const uint4 *>(dz + gp * CO + ch * 8);
+            tc_cp_async16(dz_s + p * SD + ch * 8, dz + gp * CO + ch * 8);
         }
         for (int e = tid; e < NH * (CI / 8); e += 256) {
             const int hp = e / (CI / 8), ch = e - hp * (CI / 8);
             const int hx = hp % HX, hy = (hp / HX) % HY, hz = hp / (HX * HY);
             const int gx = wrapi(x0 + hx - 1, nx), gy = wrapi(y0 + hy - 1, ny), gz = wrapi(z0 + hz - 1, nz);
             const size_t gp = ((size_t)gz * ny + gy) * nx + gx;
-            *reinterpret_cast<uint4 *>(h_s + hp * SH + ch * 8) = *reinterpret_cast<const uint4 *>(h + gp * CI + ch * 8);
+            tc_cp_async16(h_s + hp * SH + ch * 8, h + gp * CI + ch * 8);
         }
+        cp_async_wait_all();
         __syncthreads();
         if (tid < CO)
             for (int p = 0; p < NP; ++p) dbacc += bf16_val(dz_s[p * SD + tid]);
