@@ -114,6 +114,25 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *params,
 /* Frees the host metadata of a grid; never touches the caller's buffers. */
 osb_status osb_grid_destroy(osb_grid *grid);
 
+/* Boundary conditions per axis (Section 2.6, "Boundary conditions").
+ *  OSB_BC_PERIODIC (every axis after osb_grid_create): the axis is [0, 2 pi),
+ *    points x_i = 2 pi i / n, halos wrap around.
+ *  OSB_BC_SYMMETRIC: symmetry planes at both ends of the axis, at 0 and pi
+ *    (two of the Taylor-Green vortex's own mirror planes); points
+ *    x_i = (i + 1/2) pi / n.  The halo beyond the plane after the last point
+ *    mirrors the points before it, phi(x_{n+k}) = phi(x_{n-1-k}), and likewise
+ *    phi(x_{-1-k}) = phi(x_k) at the first point; the momentum component
+ *    normal to the plane changes sign there.  Every derived quantity a stage
+ *    differentiates takes the parity of its factors, so the result equals the
+ *    periodic scheme on the doubled, mirror-extended grid restricted to this
+ *    one.  osb_init_taylor_green and osb_diagnostics use these coordinates
+ *    and spacings.
+ * Symmetric grids step with the three-kernel stage in every precision; they
+ * take no learned closure and no ensemble stepping (OSB_ERR_UNSUPPORTED).
+ * Errors: OSB_ERR_INVALID_ARG (a kind other than the two above). */
+enum { OSB_BC_PERIODIC = 0, OSB_BC_SYMMETRIC = 1 };
+osb_status osb_set_boundaries(osb_grid *grid, int bc_x, int bc_y, int bc_z);
+
 /* Sets the Taylor-Green initial state of Section 3.3 (L = 1):
  *   u0 = sin x cos y cos z, u1 = -cos x sin y cos z, u2 = 0,
  *   p  = 1/(gamma M^2) + (cos 2x + cos 2y)(2 + cos 2z)/16, T = 1 (rho = gamma M^2 p),

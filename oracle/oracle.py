@@ -228,3 +228,120 @@ def diagnostics(case: Case, Q: np.ndarray) -> dict:
     g = case.c()
     lib().orc_diagnostics(ctypes.byref(g), _p(Q), _p(out))
     return dict(zip(DIAG_KEYS, out.tolist()))
+
+
+# ---------------------------------------------------------------------------
+# Symmetry boundaries (Section 2.6, "Boundary conditions").
+#
+# On an axis with symmetry planes the halo beyond the plane after the last
+# point holds the mirror image of the points before it: a scalar field keeps
+# its value, phi(x_{N+k}) = phi(x_{N-1-k}), and the component of a vector
+# field along that axis changes sign.  The same rule applies at the first
+# point, phi(x_{-1-k}) = phi(x_k).  The paper states the rule for the
+# prognostic fields; every other quantity of the scheme (velocities, pressure,
+# fluxes, their derivatives) is evaluated from those halos.  Applying the rule
+# to the conserved fields therefore turns an N-point axis into the 2N-point
+# periodic axis of the mirror-extended field, and the scheme on the symmetric
+# grid is the periodic scheme on the extended grid restricted to the first N
+# points.  The oracle below is exactly that: extend, run the periodic oracle,
+# restrict.
+#
+# Coordinates: a periodic axis is [0, 2 pi) with x_i = i h, h = 2 pi / N; a
+# symmetric axis lies between planes at 0 and pi with x_i = (i + 1/2) h,
+# h = pi / N, so its 2N-point extension is a periodic [0, 2 pi) axis with the
+# same spacing.
+# ---------------------------------------------------------------------------
+
+# sign of each conserved field (rho, rho u0, rho u1, rho u2, rho E) under the
+# mirror across a plane normal to axis 0 (x), 1 (y), 2 (z)
+SYM_PARITY = np.array([[1, 1, 1], [-1, 1, 1], [1, -1, 1], [1, 1, -1], [1, 1, 1]], dtype=np.float64)
+
+
+def sym_extend(Q: np.ndarray, sym) -> np.ndarray:
+    """Mirror-extend a (5, nz, ny, nx) state along every axis a with sym[a]
+    (Section 2.6): the appended half is the reversed field times the field's
+    parity for that axis."""
+    Q = np.asarray(Q, dtype=np.float64)
+    for a in range(3):
+        if not sym[a]:
+            continue
+        arr_axis = 3 - a  # array layout [field][z][y][x]
+        mirrored = np.flip(Q, axis=arr_axis) * SYM_PARITY[:, a].reshape(5, 1, 1, 1)
+        Q = np.concatenate([Q, mirrored], axis=arr_axis)
+    return np.ascontiguousarray(Q)
+
+
+def sym_restrict(Qe: np.ndarray, case: Case) -> np.ndarray:
+    """The first nx, ny, nz points of an extended field."""
+    return np.ascontiguousarray(Qe[..., : case.nz, : case.ny, : case.nx])
+
+
+def sym_case(case: Case, sym) -> Case:
+    """The periodic case of the extended grid (2N points on symmetric axes,
+    same spacing)."""
+    from dataclasses import replace
+    return replace(case, nx=case.nx * (2 if sym[0] else 1), ny=case.ny * (2 if sym[1] else 1),
+                   nz=case.nz * (2 if sym[2] else 1))
+
+
+def sym_residual(case: Case, Q: np.ndarray, sym) -> np.ndarray:
+    return sym_restrict(residual(sym_case(case, sym), sym_extend(Q, sym)), case)
+
+
+def sym_rk3_step(case: Case, Q: np.ndarray, nsteps: int, sym) -> np.ndarray:
+    return sym_restrict(rk3_step(sym_case(case, sym), sym_extend(Q, sym), nsteps), case)
+
+
+def sym_euler_step(case: Case, Q: np.ndarray, nsteps: int, sym) -> np.ndarray:
+    return sym_restrict(euler_step(sym_case(case, sym), sym_extend(Q, sym), nsteps), case)
+
+
+def axis_coords(n: int, symmetric: bool) -> np.ndarray:
+    """Point coordinates of one axis (see the block comment above)."""
+    i = np.arange(n, dtype=np.float64)
+    return (i + 0.5) * (np.pi / n) if symmetric else i * (2.0 * np.pi / n)
+
+
+def tgv_state(case: Case, sym=(False, False, False), noise: np.ndarray | None = None, amp: float = 0.0) -> np.ndarray:
+    """Taylor-Green initial state (Section 3.3) at the grid's points, on
+    periodic or symmetric axes; noise as in tgv_init."""
+    return tgv_at(case, axis_coords(case.nx, sym[0]), axis_coords(case.ny, sym[1]), axis_coords(case.nz, sym[2]),
+                  noise, amp)
+
+
+def tgv_at(case: Case, x: np.ndarray, y: np.ndarray, z: np.ndarray, noise: np.ndarray | None = None,
+           amp: float = 0.0) -> np.ndarray:
+    """Taylor-Green initial state (Section 3.3, T = 1 so rho = gamma M^2 p) on
+    the tensor grid of the coordinate vectors x, y, z (lengths nx, ny, nz)."""
+    X = np.asarray(x, dtype=np.float64).reshape(1, 1, -1)
+    Y = np.asarray(y, dtype=np.float64).reshape(1, -1, 1)
+    Z = np.asarray(z, dtype=np.float64).reshape(-1, 1, 1)
+    gM2 = case.gamma * case.Mach ** 2
+    shape = case.shape
+    u0 = np.broadcast_to(np.sin(X) * np.cos(Y) * np.cos(Z), shape).copy()
+    u1 = np.broadcast_to(-np.cos(X) * np.sin(Y) * np.cos(Z), shape).copy()
+    u2 = np.zeros(shape)
+    p = np.broadcast_to(1.0 / gM2 + (np.cos(2 * X) + np.cos(2 * Y)) * (2.0 + np.cos(2 * Z)) / 16.0, shape)
+    rho = gM2 * p
+    if noise is not None:
+        nz_ = np.asarray(noise, dtype=np.float64).reshape((3,) + shape)
+        u0 += amp * nz_[0]
+        u1 += amp * nz_[1]
+        u2 += amp * nz_[2]
+    return np.stack([rho, rho * u0, rho * u1, rho * u2,
+                     p / (case.gamma - 1.0) + 0.5 * rho * (u0 * u0 + u1 * u1 + u2 * u2)])
+
+
+def sym_diagnostics(case: Case, Q: np.ndarray, sym) -> dict:
+    """Diagnostics of Section 3.3 on a grid with symmetry planes: grid means
+    over this grid's points.  The enstrophy's first derivatives and the CFL
+    number come from the extended periodic grid; the kinetic energy,
+    enstrophy, CFL and non-finite count are even under every mirror, so their
+    extended-grid means equal the means here; the totals are plain means of
+    this grid's fields."""
+    d = diagnostics(sym_case(case, sym), sym_extend(Q, sym))
+    Q = np.asarray(Q, dtype=np.float64).reshape((5,) + case.shape)
+    for m, k in enumerate(("rho", "rhou0", "rhou1", "rhou2", "rhoE")):
+        d[k] = float(Q[m].mean())
+    d["nonfinite"] = float(np.count_nonzero(~np.isfinite(Q).all(axis=0)))
+    return d

@@ -12,14 +12,20 @@ namespace osb {
 //   u0 = sin x cos y cos z, u1 = -cos x sin y cos z, u2 = 0,
 //   p  = 1/(gamma M^2) + (cos 2x + cos 2y)(2 + cos 2z)/16,  T = 1 -> rho = gamma M^2 p;
 // optional u_i += amp * noise[i] at fixed rho and p.
+// Periodic axis: x_i = i h, h = 2 pi / n.  Axis between symmetry planes at 0
+// and pi (two of the vortex's own mirror planes): x_i = (i + 1/2) h, h = pi / n.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double axis_coord(int i, int n, bool sym) {
+    const double pi = 3.141592653589793238462643383279;
+    return sym ? (i + 0.5) * (pi / n) : i * (2.0 * pi / n);
+}
+
 __global__ void k_init_tgv(const Dims d, const Phys ph, double *__restrict__ U, size_t s,
                            const double *__restrict__ noise, double amp) {
-    const double two_pi = 6.283185307179586476925286766559;
-    const double hx = two_pi / d.nx, hy = two_pi / d.ny, hz = two_pi / d.nz;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
         const int x = i % d.nx, y = (i / d.nx) % d.ny, z = i / (d.nx * d.ny);
-        const double X = x * hx, Y = y * hy, Z = z * hz;
+        const double X = axis_coord(x, d.nx, d.sym & 1), Y = axis_coord(y, d.ny, d.sym & 2);
+        const double Z = axis_coord(z, d.nz, d.sym & 4);
         double sx, cx, sy, cy, sz, cz;
         sincos(X, &sx, &cx);
         sincos(Y, &sy, &cy);
@@ -136,8 +142,9 @@ __global__ void __launch_bounds__(DIAG_THREADS)
     double v[NDIAG];
 #pragma unroll
     for (int q = 0; q < NDIAG; ++q) v[q] = 0.0;
-    const double two_pi = 6.283185307179586476925286766559;
-    const double ih[3] = {d.nx / two_pi, d.ny / two_pi, d.nz / two_pi};
+    const double two_pi = 6.283185307179586476925286766559, pi = 0.5 * two_pi;
+    const double ih[3] = {d.nx / ((d.sym & 1) ? pi : two_pi), d.ny / ((d.sym & 2) ? pi : two_pi),
+                          d.nz / ((d.sym & 4) ? pi : two_pi)};
     const double *rho = U, *m0 = U + s, *m1 = U + 2 * s, *m2 = U + 3 * s, *e = U + 4 * s;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
         const int x = i % d.nx, y = (i / d.nx) % d.ny, z = i / (d.nx * d.ny);
@@ -148,9 +155,13 @@ __global__ void __launch_bounds__(DIAG_THREADS)
         int ox[2 * R + 1], oy[2 * R + 1], oz[2 * R + 1];
 #pragma unroll
         for (int k = -R; k <= R; ++k) {
-            ox[k + R] = (z * d.ny + y) * d.nx + wrapc(x + k, d.nx);
-            oy[k + R] = (z * d.ny + wrapc(y + k, d.ny)) * d.nx + x;
-            oz[k + R] = (wrapc(z + k, d.nz) * d.ny + y) * d.nx + x;
+            bool f;  // no sign: each vorticity term differentiates a velocity component even along that axis
+            const int xk = (d.sym & 1) ? mirrorc(x + k, d.nx, f) : wrapc(x + k, d.nx);
+            const int yk = (d.sym & 2) ? mirrorc(y + k, d.ny, f) : wrapc(y + k, d.ny);
+            const int zk = (d.sym & 4) ? mirrorc(z + k, d.nz, f) : wrapc(z + k, d.nz);
+            ox[k + R] = (z * d.ny + y) * d.nx + xk;
+            oy[k + R] = (z * d.ny + yk) * d.nx + x;
+            oz[k + R] = (zk * d.ny + y) * d.nx + x;
         }
         // omega = (D_y u2 - D_z u1, D_z u0 - D_x u2, D_x u1 - D_y u0)
         const double w0 = vel_d1<R>(rho, m2, oy, c.d1[1]) - vel_d1<R>(rho, m1, oz, c.d1[2]);

@@ -149,6 +149,18 @@ OrderKernels kernels_for(int order) {
     }
 }
 
+OrderKernels kernels_sym_for(int order) {
+    switch (order) {
+        case 2: return kernels_sym_o2();
+        case 4: return kernels_sym_o4();
+        case 6: return kernels_sym_o6();
+        case 8: return kernels_sym_o8();
+        case 10: return kernels_sym_o10();
+        case 12: return kernels_sym_o12();
+        default: return OrderKernels{0, nullptr, nullptr};
+    }
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no link
 // against the driver library).
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -275,12 +287,16 @@ Phys make_phys(const osb_params &prm) {
     return ph;
 }
 
-void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float> *c32) {
+// Grid spacing of an axis: periodic [0, 2 pi) with x_i = i h, or between
+// symmetry planes at 0 and pi with x_i = (i + 1/2) h.
+double axis_spacing(int n, bool symmetric) { return (symmetric ? M_PI : 2.0 * M_PI) / n; }
+
+void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float> *c32, int sym) {
     double c[MAXR + 1], dd[MAXR + 1];
     fd_weights(order, c, dd);
     const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; ++a) {
-        const double h = 2.0 * M_PI / dims[a];
+        const double h = axis_spacing(dims[a], (sym >> a) & 1);
         for (int k = 0; k <= MAXR; ++k) {
             c64->d1[a][k] = c[k] / h;
             c64->d2[a][k] = dd[k] / (h * h);
@@ -809,6 +825,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     for (int i = 0; i < n; ++i) {
         if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
         if (grids[i]->closure) return fail(OSB_ERR_UNSUPPORTED, "batch: grids with a learned closure step singly");
+        if (grids[i]->d.sym) return fail(OSB_ERR_UNSUPPORTED, "batch: grids with symmetry boundaries step singly");
     }
     const osb_grid *g0 = grids[0];
     for (int i = 1; i < n; ++i) {
@@ -958,7 +975,40 @@ osb_status osb_grid_set_closure(osb_grid *g, osb_closure *c) {
     if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
     if (c && cl::closure_points(c) != g->d.n) return fail(OSB_ERR_INVALID_ARG, "closure grid size differs from the grid's");
     if (c && g->desc.precision == OSB_DF64) return fail(OSB_ERR_UNSUPPORTED, "closures take FP64 or FP32 grids");
+    if (c && g->d.sym) return fail(OSB_ERR_UNSUPPORTED, "closures take periodic grids");
     g->closure = c;
+    return OSB_OK;
+}
+
+// Boundary kind per axis (Section 2.6).  Symmetric axes: symmetry planes at
+// 0 and pi, points at (i + 1/2) pi / n, mirrored stencil loads; periodic axes:
+// [0, 2 pi), points at 2 pi i / n.
+osb_status osb_set_boundaries(osb_grid *g, int bc_x, int bc_y, int bc_z) {
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    const int bc[3] = {bc_x, bc_y, bc_z};
+    int sym = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (bc[a] != OSB_BC_PERIODIC && bc[a] != OSB_BC_SYMMETRIC)
+            return fail(OSB_ERR_INVALID_ARG, "boundary kind must be OSB_BC_PERIODIC or OSB_BC_SYMMETRIC");
+        if (bc[a] == OSB_BC_SYMMETRIC) sym |= 1 << a;
+    }
+    if (sym && g->closure) return fail(OSB_ERR_UNSUPPORTED, "closures take periodic grids");
+    OrderKernels K = sym ? kernels_sym_for(g->desc.order) : kernels_for(g->desc.order);
+    if (!K.stage) return fail(OSB_ERR_UNSUPPORTED, "order not instantiated");
+    // captured step graphs hold the previous kernels and weights
+    for (int b = 0; b < 2; ++b)
+        if (g->step_graph[b]) {
+            cudaGraphExecDestroy(g->step_graph[b]);
+            g->step_graph[b] = nullptr;
+        }
+    g->d.sym = sym;
+    make_coefs(g->desc.order, g->desc.nx, g->desc.ny, g->desc.nz, &g->c64, &g->c32, sym);
+    make_coefs_dd(g->c64, &g->cdd);
+    g->K = K;
+    // the FP32 z-march kernels wrap periodically; symmetric grids take the
+    // three-kernel stage
+    const char *env = getenv("OSB_FP32_STAGE");
+    g->zmarch = !sym && !(env && strcmp(env, "split3") == 0);
     return OSB_OK;
 }
 

@@ -46,7 +46,8 @@ __host__ __device__ inline size_t padded(size_t n) {
 
 struct Dims {
     int nx, ny, nz;
-    int n;  // nx*ny*nz (< 2^31)
+    int n;    // nx*ny*nz (< 2^31)
+    int sym;  // bit a set: axis a has symmetry planes at both ends (Section 2.6), else periodic
 };
 
 struct Phys {
@@ -124,6 +125,13 @@ OrderKernels kernels_o6();
 OrderKernels kernels_o8();
 OrderKernels kernels_o10();
 OrderKernels kernels_o12();
+// ... and, for grids with symmetry boundaries, the mirrored-stencil variants
+OrderKernels kernels_sym_o2();
+OrderKernels kernels_sym_o4();
+OrderKernels kernels_sym_o6();
+OrderKernels kernels_sym_o8();
+OrderKernels kernels_sym_o10();
+OrderKernels kernels_sym_o12();
 
 namespace zm {
 // TMA descriptors of one z-march stage: haloed plane boxes (40 x (8 + 2R) x 1)
@@ -171,7 +179,8 @@ int closure_points(const osb_closure *c);
 
 // Host helpers shared by the translation units (defined in osb_api.cu).
 Phys make_phys(const osb_params &prm);
-void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float> *c32);
+void make_coefs(int order, int nx, int ny, int nz, Coef<double> *c64, Coef<float> *c32, int sym = 0);
+double axis_spacing(int n, bool symmetric);
 void make_coefs_dd(const Coef<double> &c64, Coef<dd> *cdd);
 void set_last_error(const char *msg);
 

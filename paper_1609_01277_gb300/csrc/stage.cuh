@@ -78,18 +78,45 @@ __device__ __forceinline__ int wrapc(int i, int n) {
     return i < 0 ? i + n : i;
 }
 
-// Wrapped neighbour offsets of one point, per axis, k = -R..R.
-template <int R>
+// Index of grid point j (any integer) on an axis of n points between two
+// symmetry planes (Section 2.6): the halo beyond the plane after the last
+// point mirrors the points before it, x_{n+k} -> x_{n-1-k}, and likewise
+// x_{-1-k} -> x_k at the first point, which makes the field the restriction
+// of a 2n-periodic, mirror-symmetric one.  refl: an odd number of mirrorings,
+// so a field that is odd in this axis changes sign.
+__device__ __forceinline__ int mirrorc(int j, int n, bool &refl) {
+    const int n2 = 2 * n;
+    int m = j % n2;
+    m = m < 0 ? m + n2 : m;
+    refl = m >= n;
+    return refl ? n2 - 1 - m : m;
+}
+
+// Neighbour offsets of one point, per axis, k = -R..R: wrapped on periodic
+// axes; with SYM, mirrored on the axes of Dims::sym, with a bit per k that
+// records the sign change of odd fields.
+template <int R, bool SYM = false>
 struct Nbr {
-    int x[2 * R + 1];  // wrapped x + k
-    int y[2 * R + 1];  // wrapped (y + k) * nx
-    int z[2 * R + 1];  // wrapped (z + k) * nx * ny
+    int x[2 * R + 1];  // x + k
+    int y[2 * R + 1];  // (y + k) * nx
+    int z[2 * R + 1];  // (z + k) * nx * ny
+    uint32_t rx = 0, ry = 0, rz = 0;  // SYM: bit k + R set where the neighbour is a mirror image
     __device__ __forceinline__ void init(int px, int py, int pz, const Dims &d) {
 #pragma unroll
         for (int k = -R; k <= R; ++k) {
-            x[k + R] = wrapc(px + k, d.nx);
-            y[k + R] = wrapc(py + k, d.ny) * d.nx;
-            z[k + R] = wrapc(pz + k, d.nz) * d.nx * d.ny;
+            if constexpr (SYM) {
+                bool fx = false, fy = false, fz = false;
+                x[k + R] = (d.sym & 1) ? mirrorc(px + k, d.nx, fx) : wrapc(px + k, d.nx);
+                y[k + R] = ((d.sym & 2) ? mirrorc(py + k, d.ny, fy) : wrapc(py + k, d.ny)) * d.nx;
+                z[k + R] = ((d.sym & 4) ? mirrorc(pz + k, d.nz, fz) : wrapc(pz + k, d.nz)) * d.nx * d.ny;
+                rx |= (uint32_t)fx << (k + R);
+                ry |= (uint32_t)fy << (k + R);
+                rz |= (uint32_t)fz << (k + R);
+            } else {
+                x[k + R] = wrapc(px + k, d.nx);
+                y[k + R] = wrapc(py + k, d.ny) * d.nx;
+                z[k + R] = wrapc(pz + k, d.nz) * d.nx * d.ny;
+            }
         }
     }
     template <int AX>
@@ -99,7 +126,29 @@ struct Nbr {
         return z[R + k] + y[R] + x[R];
     }
     __device__ __forceinline__ int center() const { return z[R] + y[R] + x[R]; }
+    // the neighbour at offset k along AX of a field with parity bits par
+    // (bit a: odd in axis a) carries a sign change
+    template <int AX>
+    __device__ __forceinline__ bool flip(int k, int par) const {
+        if constexpr (!SYM) {
+            return false;
+        } else {
+            if (!((par >> AX) & 1)) return false;
+            const uint32_t m = AX == 0 ? rx : (AX == 1 ? ry : rz);
+            return (m >> (k + R)) & 1u;
+        }
+    }
 };
+
+// Parity bits of the fields under the symmetry planes (Section 2.6: scalars
+// even, the i-th component of a vector odd along axis i); a product takes the
+// exclusive or of its factors' bits.
+enum Parity : int { PAR_EVEN = 0, PAR_X = 1, PAR_Y = 2, PAR_Z = 4, PAR_XY = 3, PAR_XZ = 5, PAR_YZ = 6 };
+
+template <typename T>
+__device__ __forceinline__ T neg_if(bool b, const T &v) {
+    return b ? -v : v;
+}
 
 // Global-load policy.  LD_NC: read-only path (data written before the launch).
 // LD_CG: L2 only, for data that other CTAs of the same (persistent) launch
@@ -120,22 +169,29 @@ __device__ __forceinline__ T ld(const P *p) {
 }
 
 // First derivative along AX of field f at the point (weights already / h).
-template <int R, int AX, int POL = LD_NC, typename T, typename P>
-__device__ __forceinline__ T D1(const P *__restrict__ f, const Nbr<R> &nb, const Coef<T> &c) {
+// par: parity bits of f (mirrored neighbours of a field odd along AX change sign).
+template <int R, int AX, int POL = LD_NC, typename T, typename P, bool SYM>
+__device__ __forceinline__ T D1(const P *__restrict__ f, const Nbr<R, SYM> &nb, const Coef<T> &c, int par = 0) {
     T s = T(0);
 #pragma unroll
-    for (int k = R; k >= 1; --k)
-        s = fma(c.d1[AX][k], ld<POL, T>(f + nb.template at<AX>(k)) - ld<POL, T>(f + nb.template at<AX>(-k)), s);
+    for (int k = R; k >= 1; --k) {
+        const T fp = neg_if(nb.template flip<AX>(k, par), ld<POL, T>(f + nb.template at<AX>(k)));
+        const T fm = neg_if(nb.template flip<AX>(-k, par), ld<POL, T>(f + nb.template at<AX>(-k)));
+        s = fma(c.d1[AX][k], fp - fm, s);
+    }
     return s;
 }
 
 // Second derivative along AX (weights already / h^2).
-template <int R, int AX, int POL = LD_NC, typename T, typename P>
-__device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R> &nb, const Coef<T> &c) {
+template <int R, int AX, int POL = LD_NC, typename T, typename P, bool SYM>
+__device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R, SYM> &nb, const Coef<T> &c, int par = 0) {
     T s = c.d2[AX][0] * ld<POL, T>(f + nb.center());
 #pragma unroll
-    for (int k = R; k >= 1; --k)
-        s = fma(c.d2[AX][k], ld<POL, T>(f + nb.template at<AX>(k)) + ld<POL, T>(f + nb.template at<AX>(-k)), s);
+    for (int k = R; k >= 1; --k) {
+        const T fp = neg_if(nb.template flip<AX>(k, par), ld<POL, T>(f + nb.template at<AX>(k)));
+        const T fm = neg_if(nb.template flip<AX>(-k, par), ld<POL, T>(f + nb.template at<AX>(-k)));
+        s = fma(c.d2[AX][k], fp + fm, s);
+    }
     return s;
 }
 
@@ -143,22 +199,26 @@ __device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R> &nb, const
 // Double-float stencils: differences (sums) of the neighbours are formed with
 // exact head arithmetic and weighted into a compensated accumulator,
 // normalised once at the end (dd_acc).
-template <int R, int AX, int POL = LD_NC, typename P>
-__device__ __forceinline__ dd D1(const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &c) {
+template <int R, int AX, int POL, typename P, bool SYM>
+__device__ __forceinline__ dd nb_ld(const P *__restrict__ f, const Nbr<R, SYM> &nb, int k, int par) {
+    return neg_if(nb.template flip<AX>(k, par), ld<POL, dd>(f + nb.template at<AX>(k)));
+}
+template <int R, int AX, int POL = LD_NC, typename P, bool SYM>
+__device__ __forceinline__ dd D1(const P *__restrict__ f, const Nbr<R, SYM> &nb, const Coef<dd> &c, int par = 0) {
     dd_acc s;
 #pragma unroll
     for (int k = R; k >= 1; --k)
-        s.add_wdiff(c.d1[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+        s.add_wdiff(c.d1[AX][k], nb_ld<R, AX, POL>(f, nb, k, par), nb_ld<R, AX, POL>(f, nb, -k, par));
     return s.get();
 }
-template <int R, int AX, int POL = LD_NC, typename P>
-__device__ __forceinline__ dd D2(const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &c) {
+template <int R, int AX, int POL = LD_NC, typename P, bool SYM>
+__device__ __forceinline__ dd D2(const P *__restrict__ f, const Nbr<R, SYM> &nb, const Coef<dd> &c, int par = 0) {
     dd_acc s;
     const dd f0 = ld<POL, dd>(f + nb.center());
     s.add_prod(c.d2[AX][0], f0.hi, f0.lo);
 #pragma unroll
     for (int k = R; k >= 1; --k)
-        s.add_wsum(c.d2[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+        s.add_wsum(c.d2[AX][k], nb_ld<R, AX, POL>(f, nb, k, par), nb_ld<R, AX, POL>(f, nb, -k, par));
     return s.get();
 }
 
@@ -273,16 +333,16 @@ __global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
 // ---------------------------------------------------------------------------
 // k_grad: velocity gradient -> div u, tau_ij, energy flux, viscous g-term
 // ---------------------------------------------------------------------------
-template <int POL, typename S, int R>
+template <int POL, typename S, int R, bool SYM>
 __device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z);
 
-template <int POL, typename S, typename T, int R, bool VB>
+template <int POL, typename S, typename T, int R, bool VB, bool SYM = false>
 __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int z) {
     if constexpr (is_dd<T> && !VB) {
-        grad_point_dd<POL, S, R>(a, x, y, z);
+        grad_point_dd<POL, S, R, SYM>(a, x, y, z);
         return;
     } else {
-    Nbr<R> nb;
+    Nbr<R, SYM> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
     const Coef<T> &c = CoefPick<T>::get(a);
@@ -290,9 +350,9 @@ __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int
     const size_t as = a.aux_stride;
     const T *U = aux + A_U * as, *V = aux + A_V * as, *W = aux + A_W * as;
 
-    const T gxx = D1<R, 0, POL>(U, nb, c), gxy = D1<R, 1, POL>(U, nb, c), gxz = D1<R, 2, POL>(U, nb, c);
-    const T gyx = D1<R, 0, POL>(V, nb, c), gyy = D1<R, 1, POL>(V, nb, c), gyz = D1<R, 2, POL>(V, nb, c);
-    const T gzx = D1<R, 0, POL>(W, nb, c), gzy = D1<R, 1, POL>(W, nb, c), gzz = D1<R, 2, POL>(W, nb, c);
+    const T gxx = D1<R, 0, POL>(U, nb, c, PAR_X), gxy = D1<R, 1, POL>(U, nb, c, PAR_X), gxz = D1<R, 2, POL>(U, nb, c, PAR_X);
+    const T gyx = D1<R, 0, POL>(V, nb, c, PAR_Y), gyy = D1<R, 1, POL>(V, nb, c, PAR_Y), gyz = D1<R, 2, POL>(V, nb, c, PAR_Y);
+    const T gzx = D1<R, 0, POL>(W, nb, c, PAR_Z), gzy = D1<R, 1, POL>(W, nb, c, PAR_Z), gzz = D1<R, 2, POL>(W, nb, c, PAR_Z);
     const T div = gxx + gyy + gzz;
     const T ir = k_inv_re<T>(a);
     const T tdiv = T(2.0 / 3.0) * div;
@@ -330,18 +390,18 @@ __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int
 // accumulated compensated; likewise Phi_ii - (1/(3Re)) sum_{k != i} g_kk.
 __device__ __forceinline__ void acc_add(dd_acc &acc, const dd &w, const dd &x) { acc.add_prod(w, x.hi, x.lo); }
 
-template <int POL, typename S, int R>
+template <int POL, typename S, int R, bool SYM>
 __device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z) {
-    Nbr<R> nb;
+    Nbr<R, SYM> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
     const Coef<dd> &c = a.cdd;
     dd *aux = static_cast<dd *>(a.aux);
     const size_t as = a.aux_stride;
     const dd *U = aux + A_U * as, *V = aux + A_V * as, *W = aux + A_W * as;
-    const dd gxx = D1<R, 0, POL>(U, nb, c), gxy = D1<R, 1, POL>(U, nb, c), gxz = D1<R, 2, POL>(U, nb, c);
-    const dd gyx = D1<R, 0, POL>(V, nb, c), gyy = D1<R, 1, POL>(V, nb, c), gyz = D1<R, 2, POL>(V, nb, c);
-    const dd gzx = D1<R, 0, POL>(W, nb, c), gzy = D1<R, 1, POL>(W, nb, c), gzz = D1<R, 2, POL>(W, nb, c);
+    const dd gxx = D1<R, 0, POL>(U, nb, c, PAR_X), gxy = D1<R, 1, POL>(U, nb, c, PAR_X), gxz = D1<R, 2, POL>(U, nb, c, PAR_X);
+    const dd gyx = D1<R, 0, POL>(V, nb, c, PAR_Y), gyy = D1<R, 1, POL>(V, nb, c, PAR_Y), gyz = D1<R, 2, POL>(V, nb, c, PAR_Y);
+    const dd gzx = D1<R, 0, POL>(W, nb, c, PAR_Z), gzy = D1<R, 1, POL>(W, nb, c, PAR_Z), gzz = D1<R, 2, POL>(W, nb, c, PAR_Z);
     dd_acc dv;
     const dd one(1.f, 0.f);
     acc_add(dv, one, gxx);
@@ -400,11 +460,11 @@ __device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, 
     aux[A_PZZ * as + i] = pz.get();
 }
 
-template <typename S, typename T, int R, bool VB>
+template <typename S, typename T, int R, bool VB, bool SYM>
 __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
     if (x >= a.d.nx || y >= a.d.ny) return;
-    grad_point<LD_NC, S, T, R, VB>(a, x, y, z);
+    grad_point<LD_NC, S, T, R, VB, SYM>(a, x, y, z);
 }
 
 // ---------------------------------------------------------------------------
@@ -413,26 +473,29 @@ __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
 // their constant factors folded into the stencil weights, the advective
 // products as products -- normalised once per equation.
 // ---------------------------------------------------------------------------
-template <int R, int AX, int POL, typename P>
-__device__ __forceinline__ void acc_d1(dd_acc &acc, const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &w,
-                                       bool negate) {
+template <int R, int AX, int POL, typename P, bool SYM>
+__device__ __forceinline__ void acc_d1(dd_acc &acc, const P *__restrict__ f, const Nbr<R, SYM> &nb, const Coef<dd> &w,
+                                       bool negate, int par) {
 #pragma unroll
     for (int k = R; k >= 1; --k) {
         const dd wk = negate ? -w.d1[AX][k] : w.d1[AX][k];
-        acc.add_wdiff(wk, ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+        acc.add_wdiff(wk, nb_ld<R, AX, POL>(f, nb, k, par), nb_ld<R, AX, POL>(f, nb, -k, par));
     }
 }
-template <int R, int AX, int POL, typename P>
-__device__ __forceinline__ void acc_d2(dd_acc &acc, const P *__restrict__ f, const Nbr<R> &nb, const Coef<dd> &w,
-                                       const dd &f0) {
+template <int R, int AX, int POL, typename P, bool SYM>
+__device__ __forceinline__ void acc_d2(dd_acc &acc, const P *__restrict__ f, const Nbr<R, SYM> &nb, const Coef<dd> &w,
+                                       const dd &f0, int par) {
     acc.add_prod(w.d2[AX][0], f0.hi, f0.lo);
 #pragma unroll
     for (int k = R; k >= 1; --k)
-        acc.add_wsum(w.d2[AX][k], ld<POL, dd>(f + nb.template at<AX>(k)), ld<POL, dd>(f + nb.template at<AX>(-k)));
+        acc.add_wsum(w.d2[AX][k], nb_ld<R, AX, POL>(f, nb, k, par), nb_ld<R, AX, POL>(f, nb, -k, par));
 }
 
-template <int POL, typename S, int R, bool VB>
-__device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> &nb, int i, dd (&res)[5]) {
+// parity bits of the conserved fields rho, rho u, rho v, rho w, rho E
+__device__ __forceinline__ constexpr int q_parity(int m) { return m == 1 ? PAR_X : (m == 2 ? PAR_Y : (m == 3 ? PAR_Z : PAR_EVEN)); }
+
+template <int POL, typename S, int R, bool VB, bool SYM>
+__device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R, SYM> &nb, int i, dd (&res)[5]) {
     const Coef<dd> &c = a.cdd;
     const S *Q = static_cast<const S *>(a.src);
     const size_t qs = a.src_stride;
@@ -446,7 +509,8 @@ __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> 
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
         const S *f = Q + m * qs;
-        const dd dx = D1<R, 0, POL>(f, nb, c), dy = D1<R, 1, POL>(f, nb, c), dz = D1<R, 2, POL>(f, nb, c);
+        const int pm = q_parity(m);
+        const dd dx = D1<R, 0, POL>(f, nb, c, pm), dy = D1<R, 1, POL>(f, nb, c, pm), dz = D1<R, 2, POL>(f, nb, c, pm);
         acc[m].add_prod(hu, dx.hi, dx.lo);
         acc[m].add_prod(hv, dy.hi, dy.lo);
         acc[m].add_prod(hw, dz.hi, dz.lo);
@@ -460,47 +524,47 @@ __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> 
     // momentum fluxes -D_j Phi_ij and energy flux -D_j F'_j - c_ref div u
     const dd *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
     const dd *Pxy = aux + A_PXY * as, *Pxz = aux + A_PXZ * as, *Pyz = aux + A_PYZ * as;
-    acc_d1<R, 0, POL>(acc[1], Pxx, nb, c, true);
-    acc_d1<R, 1, POL>(acc[1], Pxy, nb, c, true);
-    acc_d1<R, 2, POL>(acc[1], Pxz, nb, c, true);
-    acc_d1<R, 0, POL>(acc[2], Pxy, nb, c, true);
-    acc_d1<R, 1, POL>(acc[2], Pyy, nb, c, true);
-    acc_d1<R, 2, POL>(acc[2], Pyz, nb, c, true);
-    acc_d1<R, 0, POL>(acc[3], Pxz, nb, c, true);
-    acc_d1<R, 1, POL>(acc[3], Pyz, nb, c, true);
-    acc_d1<R, 2, POL>(acc[3], Pzz, nb, c, true);
-    acc_d1<R, 0, POL>(acc[4], aux + A_FX * as, nb, c, true);
-    acc_d1<R, 1, POL>(acc[4], aux + A_FY * as, nb, c, true);
-    acc_d1<R, 2, POL>(acc[4], aux + A_FZ * as, nb, c, true);
+    acc_d1<R, 0, POL>(acc[1], Pxx, nb, c, true, PAR_EVEN);
+    acc_d1<R, 1, POL>(acc[1], Pxy, nb, c, true, PAR_XY);
+    acc_d1<R, 2, POL>(acc[1], Pxz, nb, c, true, PAR_XZ);
+    acc_d1<R, 0, POL>(acc[2], Pxy, nb, c, true, PAR_XY);
+    acc_d1<R, 1, POL>(acc[2], Pyy, nb, c, true, PAR_EVEN);
+    acc_d1<R, 2, POL>(acc[2], Pyz, nb, c, true, PAR_YZ);
+    acc_d1<R, 0, POL>(acc[3], Pxz, nb, c, true, PAR_XZ);
+    acc_d1<R, 1, POL>(acc[3], Pyz, nb, c, true, PAR_YZ);
+    acc_d1<R, 2, POL>(acc[3], Pzz, nb, c, true, PAR_EVEN);
+    acc_d1<R, 0, POL>(acc[4], aux + A_FX * as, nb, c, true, PAR_X);
+    acc_d1<R, 1, POL>(acc[4], aux + A_FY * as, nb, c, true, PAR_Y);
+    acc_d1<R, 2, POL>(acc[4], aux + A_FZ * as, nb, c, true, PAR_Z);
     acc[4].add_prod(-a.kdd.c_ref, div.hi, div.lo);
     // viscous Laplacians (1/Re)[sum_j L_j u_i + L_i u_i / 3]
     const dd *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as;
     if (!VB) {
-        acc_d2<R, 0, POL>(acc[1], Uf, nb, a.cdd_vis43, u);
-        acc_d2<R, 1, POL>(acc[1], Uf, nb, a.cdd_vis, u);
-        acc_d2<R, 2, POL>(acc[1], Uf, nb, a.cdd_vis, u);
-        acc_d2<R, 0, POL>(acc[2], Vf, nb, a.cdd_vis, v);
-        acc_d2<R, 1, POL>(acc[2], Vf, nb, a.cdd_vis43, v);
-        acc_d2<R, 2, POL>(acc[2], Vf, nb, a.cdd_vis, v);
-        acc_d2<R, 0, POL>(acc[3], Wf, nb, a.cdd_vis, w);
-        acc_d2<R, 1, POL>(acc[3], Wf, nb, a.cdd_vis, w);
-        acc_d2<R, 2, POL>(acc[3], Wf, nb, a.cdd_vis43, w);
+        acc_d2<R, 0, POL>(acc[1], Uf, nb, a.cdd_vis43, u, PAR_X);
+        acc_d2<R, 1, POL>(acc[1], Uf, nb, a.cdd_vis, u, PAR_X);
+        acc_d2<R, 2, POL>(acc[1], Uf, nb, a.cdd_vis, u, PAR_X);
+        acc_d2<R, 0, POL>(acc[2], Vf, nb, a.cdd_vis, v, PAR_Y);
+        acc_d2<R, 1, POL>(acc[2], Vf, nb, a.cdd_vis43, v, PAR_Y);
+        acc_d2<R, 2, POL>(acc[2], Vf, nb, a.cdd_vis, v, PAR_Y);
+        acc_d2<R, 0, POL>(acc[3], Wf, nb, a.cdd_vis, w, PAR_Z);
+        acc_d2<R, 1, POL>(acc[3], Wf, nb, a.cdd_vis, w, PAR_Z);
+        acc_d2<R, 2, POL>(acc[3], Wf, nb, a.cdd_vis43, w, PAR_Z);
     } else {
         // form B: the viscous momentum term (with D_i g_i / 3) is also needed
         // as a value for the work u_i (viscous term) + tau : grad u
         dd_acc vx, vy, vz;
-        acc_d2<R, 0, POL>(vx, Uf, nb, a.cdd_vis43, u);
-        acc_d2<R, 1, POL>(vx, Uf, nb, a.cdd_vis, u);
-        acc_d2<R, 2, POL>(vx, Uf, nb, a.cdd_vis, u);
-        acc_d1<R, 0, POL>(vx, aux + A_GX * as, nb, a.cdd_g, false);
-        acc_d2<R, 0, POL>(vy, Vf, nb, a.cdd_vis, v);
-        acc_d2<R, 1, POL>(vy, Vf, nb, a.cdd_vis43, v);
-        acc_d2<R, 2, POL>(vy, Vf, nb, a.cdd_vis, v);
-        acc_d1<R, 1, POL>(vy, aux + A_GY * as, nb, a.cdd_g, false);
-        acc_d2<R, 0, POL>(vz, Wf, nb, a.cdd_vis, w);
-        acc_d2<R, 1, POL>(vz, Wf, nb, a.cdd_vis, w);
-        acc_d2<R, 2, POL>(vz, Wf, nb, a.cdd_vis43, w);
-        acc_d1<R, 2, POL>(vz, aux + A_GZ * as, nb, a.cdd_g, false);
+        acc_d2<R, 0, POL>(vx, Uf, nb, a.cdd_vis43, u, PAR_X);
+        acc_d2<R, 1, POL>(vx, Uf, nb, a.cdd_vis, u, PAR_X);
+        acc_d2<R, 2, POL>(vx, Uf, nb, a.cdd_vis, u, PAR_X);
+        acc_d1<R, 0, POL>(vx, aux + A_GX * as, nb, a.cdd_g, false, PAR_EVEN);
+        acc_d2<R, 0, POL>(vy, Vf, nb, a.cdd_vis, v, PAR_Y);
+        acc_d2<R, 1, POL>(vy, Vf, nb, a.cdd_vis43, v, PAR_Y);
+        acc_d2<R, 2, POL>(vy, Vf, nb, a.cdd_vis, v, PAR_Y);
+        acc_d1<R, 1, POL>(vy, aux + A_GY * as, nb, a.cdd_g, false, PAR_EVEN);
+        acc_d2<R, 0, POL>(vz, Wf, nb, a.cdd_vis, w, PAR_Z);
+        acc_d2<R, 1, POL>(vz, Wf, nb, a.cdd_vis, w, PAR_Z);
+        acc_d2<R, 2, POL>(vz, Wf, nb, a.cdd_vis43, w, PAR_Z);
+        acc_d1<R, 2, POL>(vz, aux + A_GZ * as, nb, a.cdd_g, false, PAR_EVEN);
         const dd VX = vx.get(), VY = vy.get(), VZ = vz.get();
         acc[1].add_prod(dd(1.f, 0.f), VX.hi, VX.lo);
         acc[2].add_prod(dd(1.f, 0.f), VY.hi, VY.lo);
@@ -514,9 +578,9 @@ __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> 
     // heat flux kappa sum_j L_j T
     const dd *Tf = aux + A_T * as;
     const dd T0 = ld<POL, dd>(Tf + i);
-    acc_d2<R, 0, POL>(acc[4], Tf, nb, a.cdd_heat, T0);
-    acc_d2<R, 1, POL>(acc[4], Tf, nb, a.cdd_heat, T0);
-    acc_d2<R, 2, POL>(acc[4], Tf, nb, a.cdd_heat, T0);
+    acc_d2<R, 0, POL>(acc[4], Tf, nb, a.cdd_heat, T0, PAR_EVEN);
+    acc_d2<R, 1, POL>(acc[4], Tf, nb, a.cdd_heat, T0, PAR_EVEN);
+    acc_d2<R, 2, POL>(acc[4], Tf, nb, a.cdd_heat, T0, PAR_EVEN);
 #pragma unroll
     for (int m = 0; m < 5; ++m) res[m] = acc[m].get();
 }
@@ -524,9 +588,9 @@ __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R> 
 // ---------------------------------------------------------------------------
 // k_resid: residual and RK update (MODE 0) or residual only (MODE 1)
 // ---------------------------------------------------------------------------
-template <int POL, typename S, typename T, int R, int MODE, bool VB>
+template <int POL, typename S, typename T, int R, int MODE, bool VB, bool SYM = false>
 __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, int z) {
-    Nbr<R> nb;
+    Nbr<R, SYM> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
     const Coef<T> &c = CoefPick<T>::get(a);
@@ -537,7 +601,7 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
 
     T res[5];
     if constexpr (is_dd<T>) {
-        resid_terms_dd<POL, S, R, VB>(a, nb, i, res);
+        resid_terms_dd<POL, S, R, VB, SYM>(a, nb, i, res);
     } else {
     const T u = ld<POL, T>(aux + A_U * as + i), v = ld<POL, T>(aux + A_V * as + i);
     const T w = ld<POL, T>(aux + A_W * as + i), div = ld<POL, T>(aux + A_DIV * as + i);
@@ -546,7 +610,8 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
         const S *f = Q + m * qs;
-        const T dx = D1<R, 0, POL>(f, nb, c), dy = D1<R, 1, POL>(f, nb, c), dz = D1<R, 2, POL>(f, nb, c);
+        const int pm = q_parity(m);
+        const T dx = D1<R, 0, POL>(f, nb, c, pm), dy = D1<R, 1, POL>(f, nb, c, pm), dz = D1<R, 2, POL>(f, nb, c, pm);
         T qc = ld<POL, T>(f + i);
         if constexpr (is_dd<T>) {
             if (m == 4) qc = qc + a.kdd.e_ref;  // the full rho E multiplies div u
@@ -560,12 +625,12 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     // momentum fluxes
     const T *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
     const T *Pxy = aux + A_PXY * as, *Pxz = aux + A_PXZ * as, *Pyz = aux + A_PYZ * as;
-    res[1] -= D1<R, 0, POL>(Pxx, nb, c) + D1<R, 1, POL>(Pxy, nb, c) + D1<R, 2, POL>(Pxz, nb, c);
-    res[2] -= D1<R, 0, POL>(Pxy, nb, c) + D1<R, 1, POL>(Pyy, nb, c) + D1<R, 2, POL>(Pyz, nb, c);
-    res[3] -= D1<R, 0, POL>(Pxz, nb, c) + D1<R, 1, POL>(Pyz, nb, c) + D1<R, 2, POL>(Pzz, nb, c);
+    res[1] -= D1<R, 0, POL>(Pxx, nb, c) + D1<R, 1, POL>(Pxy, nb, c, PAR_XY) + D1<R, 2, POL>(Pxz, nb, c, PAR_XZ);
+    res[2] -= D1<R, 0, POL>(Pxy, nb, c, PAR_XY) + D1<R, 1, POL>(Pyy, nb, c) + D1<R, 2, POL>(Pyz, nb, c, PAR_YZ);
+    res[3] -= D1<R, 0, POL>(Pxz, nb, c, PAR_XZ) + D1<R, 1, POL>(Pyz, nb, c, PAR_YZ) + D1<R, 2, POL>(Pzz, nb, c);
     // energy flux
-    res[4] -= D1<R, 0, POL>(aux + A_FX * as, nb, c) + D1<R, 1, POL>(aux + A_FY * as, nb, c) +
-              D1<R, 2, POL>(aux + A_FZ * as, nb, c);
+    res[4] -= D1<R, 0, POL>(aux + A_FX * as, nb, c, PAR_X) + D1<R, 1, POL>(aux + A_FY * as, nb, c, PAR_Y) +
+              D1<R, 2, POL>(aux + A_FZ * as, nb, c, PAR_Z);
     if constexpr (is_dd<T>) {
         // F_j = F'_j + (e_ref/2 + p_ref) u_j with F'_j built from the deviations
         res[4] -= a.kdd.c_ref * div;
@@ -574,9 +639,9 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     const T ir = k_inv_re<T>(a), f43 = T(4.0 / 3.0);
     {
         const T *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as;
-        T vx = ir * fma(f43, D2<R, 0, POL>(Uf, nb, c), D2<R, 1, POL>(Uf, nb, c) + D2<R, 2, POL>(Uf, nb, c));
-        T vy = ir * fma(f43, D2<R, 1, POL>(Vf, nb, c), D2<R, 0, POL>(Vf, nb, c) + D2<R, 2, POL>(Vf, nb, c));
-        T vz = ir * fma(f43, D2<R, 2, POL>(Wf, nb, c), D2<R, 0, POL>(Wf, nb, c) + D2<R, 1, POL>(Wf, nb, c));
+        T vx = ir * fma(f43, D2<R, 0, POL>(Uf, nb, c, PAR_X), D2<R, 1, POL>(Uf, nb, c, PAR_X) + D2<R, 2, POL>(Uf, nb, c, PAR_X));
+        T vy = ir * fma(f43, D2<R, 1, POL>(Vf, nb, c, PAR_Y), D2<R, 0, POL>(Vf, nb, c, PAR_Y) + D2<R, 2, POL>(Vf, nb, c, PAR_Y));
+        T vz = ir * fma(f43, D2<R, 2, POL>(Wf, nb, c, PAR_Z), D2<R, 0, POL>(Wf, nb, c, PAR_Z) + D2<R, 1, POL>(Wf, nb, c, PAR_Z));
         if (VB) {
             // the D_i g_i / 3 part of the viscous momentum term, kept separate
             const T ir3 = ir * T(1.0 / 3.0);
@@ -635,69 +700,70 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     }
 }
 
-template <typename S, typename T, int R, int MODE, bool VB>
+template <typename S, typename T, int R, int MODE, bool VB, bool SYM>
 __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
     if (x >= a.d.nx || y >= a.d.ny) return;
-    resid_point<LD_NC, S, T, R, MODE, VB>(a, x, y, z);
+    resid_point<LD_NC, S, T, R, MODE, VB, SYM>(a, x, y, z);
 }
 
 // Double-float residual kernel with explicit occupancy targets: three CTAs per
 // SM up to order 4 (a few spilled registers buy 24 resident warps to hide the
 // neighbour-load latency this kernel waits on), two for orders 6 and 8, one
 // (all registers, no spills) for orders 10 and 12.
-template <typename S, int R, int MODE, bool VB>
+template <typename S, int R, int MODE, bool VB, bool SYM>
 __global__ void __launch_bounds__(BX *BY, R <= 2 ? 3 : (R <= 4 ? 2 : 1)) k_resid_dd(const StageArgs a) {
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
     if (x >= a.d.nx || y >= a.d.ny) return;
-    resid_point<LD_NC, S, dd, R, MODE, VB>(a, x, y, z);
+    resid_point<LD_NC, S, dd, R, MODE, VB, SYM>(a, x, y, z);
 }
 
-template <typename S, typename T, int R, bool VB>
+// SYM: the mirrored-stencil kernels for grids with symmetry boundaries.
+template <typename S, typename T, int R, bool VB, bool SYM>
 cudaError_t launch_stage_typed(const StageArgs &a, int mode) {
     dim3 blk(BX, BY, 1), grd((a.d.nx + BX - 1) / BX, (a.d.ny + BY - 1) / BY, a.d.nz);
     if (a.ev) cudaEventRecord(a.ev[0], a.stream);
     k_prim<S, T><<<grd, blk, 0, a.stream>>>(a);
     if (a.ev) cudaEventRecord(a.ev[1], a.stream);
-    k_grad<S, T, R, VB><<<grd, blk, 0, a.stream>>>(a);
+    k_grad<S, T, R, VB, SYM><<<grd, blk, 0, a.stream>>>(a);
     if (a.ev) cudaEventRecord(a.ev[2], a.stream);
     if constexpr (is_dd<T>) {
         if (mode == 0)
-            k_resid_dd<S, R, 0, VB><<<grd, blk, 0, a.stream>>>(a);
+            k_resid_dd<S, R, 0, VB, SYM><<<grd, blk, 0, a.stream>>>(a);
         else
-            k_resid_dd<S, R, 1, VB><<<grd, blk, 0, a.stream>>>(a);
+            k_resid_dd<S, R, 1, VB, SYM><<<grd, blk, 0, a.stream>>>(a);
     } else {
         if (mode == 0)
-            k_resid<S, T, R, 0, VB><<<grd, blk, 0, a.stream>>>(a);
+            k_resid<S, T, R, 0, VB, SYM><<<grd, blk, 0, a.stream>>>(a);
         else
-            k_resid<S, T, R, 1, VB><<<grd, blk, 0, a.stream>>>(a);
+            k_resid<S, T, R, 1, VB, SYM><<<grd, blk, 0, a.stream>>>(a);
     }
     if (a.ev) cudaEventRecord(a.ev[3], a.stream);
     return cudaGetLastError();
 }
 
-template <typename S, typename T, int R>
+template <typename S, typename T, int R, bool SYM>
 cudaError_t launch_stage_form(const StageArgs &a, int mode) {
-    if (a.visc_form == OSB_VISC_B) return launch_stage_typed<S, T, R, true>(a, mode);
-    return launch_stage_typed<S, T, R, false>(a, mode);
+    if (a.visc_form == OSB_VISC_B) return launch_stage_typed<S, T, R, true, SYM>(a, mode);
+    return launch_stage_typed<S, T, R, false, SYM>(a, mode);
 }
 
-template <int R>
+template <int R, bool SYM = false>
 cudaError_t launch_stage(const StageArgs &a, int mode) {
-    if (a.precision == OSB_FP64) return launch_stage_form<double, double, R>(a, mode);
+    if (a.precision == OSB_FP64) return launch_stage_form<double, double, R, SYM>(a, mode);
     if (a.precision == OSB_DF64)
-        return a.src_is_f64 ? launch_stage_form<double, dd, R>(a, mode) : launch_stage_form<dd, dd, R>(a, mode);
-    if (a.src_is_f64) return launch_stage_form<double, float, R>(a, mode);
-    return launch_stage_form<float, float, R>(a, mode);
+        return a.src_is_f64 ? launch_stage_form<double, dd, R, SYM>(a, mode) : launch_stage_form<dd, dd, R, SYM>(a, mode);
+    if (a.src_is_f64) return launch_stage_form<double, float, R, SYM>(a, mode);
+    return launch_stage_form<float, float, R, SYM>(a, mode);
 }
 
-template <int R>
+template <int R, bool SYM = false>
 cudaError_t stage_entry(const StageArgs &a) {
-    return launch_stage<R>(a, 0);
+    return launch_stage<R, SYM>(a, 0);
 }
-template <int R>
+template <int R, bool SYM = false>
 cudaError_t residual_entry(const StageArgs &a) {
-    return launch_stage<R>(a, 1);
+    return launch_stage<R, SYM>(a, 1);
 }
 
 }  // namespace osb
@@ -707,4 +773,13 @@ cudaError_t residual_entry(const StageArgs &a) {
     OrderKernels kernels_o##ORDER() {                                          \
         return OrderKernels{ORDER, &stage_entry<ORDER / 2>, &residual_entry<ORDER / 2>}; \
     }                                                                          \
+    }
+
+// Grids with symmetry boundaries: the three-kernel stage with mirrored
+// neighbour loads, in every precision.
+#define OSB_DEFINE_ORDER_SYM(ORDER)                                                         \
+    namespace osb {                                                                        \
+    OrderKernels kernels_sym_o##ORDER() {                                                  \
+        return OrderKernels{ORDER, &stage_entry<ORDER / 2, true>, &residual_entry<ORDER / 2, true>}; \
+    }                                                                                      \
     }

@@ -20,6 +20,7 @@ LIB_PATH = _build.LIB
 
 OSB_FP64, OSB_FP32, OSB_DF64 = 0, 1, 2
 OSB_VISC_A, OSB_VISC_B = 0, 1
+OSB_BC_PERIODIC, OSB_BC_SYMMETRIC = 0, 1
 STATUS = {0: "OSB_OK", 1: "OSB_ERR_INVALID_ARG", 2: "OSB_ERR_UNSUPPORTED", 3: "OSB_ERR_CUDA",
           4: "OSB_ERR_NONFINITE", 5: "OSB_ERR_TIMEOUT", 6: "OSB_ERR_BUFFER"}
 
@@ -32,7 +33,7 @@ EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_gri
            "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_closure_create", "osb_closure_destroy",
            "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_set_dissipative", "osb_closure_set_loss_weight", "osb_closure_status", "osb_closure_sync_weights",
            "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
-           "osb_box_filter", "osb_scalar_rk3", "osb_profile_start", "osb_profile_stop",
+           "osb_box_filter", "osb_scalar_rk3", "osb_set_boundaries", "osb_profile_start", "osb_profile_stop",
            "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
@@ -94,6 +95,7 @@ def load(path: str | None = None):
     L.osb_diagnostics_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, vp, vp]
     L.osb_scalar_rk3.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
+    L.osb_set_boundaries.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.osb_profile_start.argtypes = [vp, ctypes.c_int]
     L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.osb_status_string.argtypes = [ctypes.c_int]
@@ -125,6 +127,9 @@ class Config:
     gamma: float = 1.4
     Pr: float = 0.71
     dt: float = 3.385e-3
+    # boundary kind per axis (x, y, z): OSB_BC_PERIODIC, or OSB_BC_SYMMETRIC
+    # (symmetry planes at 0 and pi, points at (i + 1/2) pi / n)
+    bc: tuple = (OSB_BC_PERIODIC, OSB_BC_PERIODIC, OSB_BC_PERIODIC)
 
     def desc(self) -> GridDesc:
         return GridDesc(self.nx, self.ny, self.nz, self.order, self.precision, self.visc_form)
@@ -142,7 +147,8 @@ class Config:
 
 
 class Grid:
-    """One periodic grid on the current CUDA device, advanced on one stream."""
+    """One grid on the current CUDA device, advanced on one stream; periodic,
+    or with symmetry planes on the axes that ``cfg.bc`` marks."""
 
     def __init__(self, cfg: Config, stream=None, device=None):
         import torch
@@ -164,6 +170,8 @@ class Grid:
                                 self.workspace.data_ptr(), wb, self.stream.cuda_stream, ctypes.byref(h)),
               "osb_grid_create")
         self.handle = h
+        if any(b != OSB_BC_PERIODIC for b in cfg.bc):
+            check(L.osb_set_boundaries(h, *[int(b) for b in cfg.bc]), "osb_set_boundaries")
 
     def close(self):
         if getattr(self, "handle", None):
