@@ -258,6 +258,35 @@ StageArgs base_args(const osb_grid *g) {
                 a.cdd_g.d1[ax][k] = dd(ir * (1.0 / 3.0) * d1);
             }
     }
+    {
+        const double ir = g->ph.inv_re, kap = g->ph.kappa;
+        FoldW<double> &f = a.f64;
+        for (int ax = 0; ax < 3; ++ax)
+            for (int k = 0; k <= MAXR; ++k) {
+                const double d2 = g->c64.d2[ax][k], d1 = g->c64.d1[ax][k];
+                f.vis[ax][k] = ir * d2;
+                f.vis43[ax][k] = ir * (4.0 / 3.0) * d2;
+                f.heat[ax][k] = kap * d2;
+                f.g[ax][k] = ir * (1.0 / 3.0) * d1;
+            }
+        const double d0x = g->c64.d2[0][0], d0y = g->c64.d2[1][0], d0z = g->c64.d2[2][0];
+        f.c_u = ir * ((4.0 / 3.0) * d0x + d0y + d0z);
+        f.c_v = ir * (d0x + (4.0 / 3.0) * d0y + d0z);
+        f.c_w = ir * (d0x + d0y + (4.0 / 3.0) * d0z);
+        f.c_T = kap * (d0x + d0y + d0z);
+        FoldW<float> &h = a.f32;
+        for (int ax = 0; ax < 3; ++ax)
+            for (int k = 0; k <= MAXR; ++k) {
+                h.vis[ax][k] = (float)f.vis[ax][k];
+                h.vis43[ax][k] = (float)f.vis43[ax][k];
+                h.heat[ax][k] = (float)f.heat[ax][k];
+                h.g[ax][k] = (float)f.g[ax][k];
+            }
+        h.c_u = (float)f.c_u;
+        h.c_v = (float)f.c_v;
+        h.c_w = (float)f.c_w;
+        h.c_T = (float)f.c_T;
+    }
     a.precision = g->desc.precision;
     a.visc_form = g->desc.visc_form;
     a.zmarch = g->zmarch;

@@ -63,6 +63,17 @@ struct Coef {
     T d2[3][MAXR + 1];
 };
 
+// Folded weights of the FP64 / FP32 residual: second-derivative weights
+// scaled by 1/Re (vis), 4/(3 Re) (vis43) and kappa (heat), first-derivative
+// weights by 1/(3 Re) (g, viscous form B), and the centre weights of the three
+// viscous Laplacians and of the heat-flux Laplacian summed over the axes, so
+// that each equation's terms accumulate with one FMA per stencil tap.
+template <typename T>
+struct FoldW {
+    T vis[3][MAXR + 1], vis43[3][MAXR + 1], heat[3][MAXR + 1], g[3][MAXR + 1];
+    T c_u, c_v, c_w, c_T;  // centre: (1/Re)(4/3 d0_x + d0_y + d0_z), ..., kappa (d0_x + d0_y + d0_z)
+};
+
 // Everything a stage launch needs.
 struct StageArgs {
     Dims d;
@@ -83,6 +94,8 @@ struct StageArgs {
     // kappa, first-derivative weights by 1/(3 Re), so each equation's terms
     // accumulate without separate multiplications
     Coef<dd> cdd_vis, cdd_vis43, cdd_heat, cdd_g;
+    FoldW<double> f64;
+    FoldW<float> f32;
     int precision;          // OSB_FP64 / OSB_FP32 / OSB_DF64
     int visc_form;          // OSB_VISC_A / OSB_VISC_B
     const void *src;        // stencil source q_{k-1}

@@ -54,6 +54,17 @@ struct CoefPick<dd> {
 template <typename T>
 constexpr bool is_dd = std::is_same<T, dd>::value;
 
+template <typename T>
+struct FoldPick;
+template <>
+struct FoldPick<double> {
+    static __device__ __forceinline__ const FoldW<double> &get(const StageArgs &a) { return a.f64; }
+};
+template <>
+struct FoldPick<float> {
+    static __device__ __forceinline__ const FoldW<float> &get(const StageArgs &a) { return a.f32; }
+};
+
 // Physical constants in the arithmetic type (double-float ones precomputed on
 // the host, so no kernel converts them).
 template <typename T>
@@ -95,12 +106,18 @@ __device__ __forceinline__ int mirrorc(int j, int n, bool &refl) {
 // Neighbour offsets of one point, per axis, k = -R..R: wrapped on periodic
 // axes; with SYM, mirrored on the axes of Dims::sym, with a bit per k that
 // records the sign change of odd fields.
+template <bool SYM>
+struct NbrMask {
+    uint32_t rx = 0, ry = 0, rz = 0;  // bit k + R set where the neighbour is a mirror image
+};
+template <>
+struct NbrMask<false> {};
+
 template <int R, bool SYM = false>
-struct Nbr {
+struct Nbr : NbrMask<SYM> {
     int x[2 * R + 1];  // x + k
     int y[2 * R + 1];  // (y + k) * nx
     int z[2 * R + 1];  // (z + k) * nx * ny
-    uint32_t rx = 0, ry = 0, rz = 0;  // SYM: bit k + R set where the neighbour is a mirror image
     __device__ __forceinline__ void init(int px, int py, int pz, const Dims &d) {
 #pragma unroll
         for (int k = -R; k <= R; ++k) {
@@ -109,9 +126,9 @@ struct Nbr {
                 x[k + R] = (d.sym & 1) ? mirrorc(px + k, d.nx, fx) : wrapc(px + k, d.nx);
                 y[k + R] = ((d.sym & 2) ? mirrorc(py + k, d.ny, fy) : wrapc(py + k, d.ny)) * d.nx;
                 z[k + R] = ((d.sym & 4) ? mirrorc(pz + k, d.nz, fz) : wrapc(pz + k, d.nz)) * d.nx * d.ny;
-                rx |= (uint32_t)fx << (k + R);
-                ry |= (uint32_t)fy << (k + R);
-                rz |= (uint32_t)fz << (k + R);
+                this->rx |= (uint32_t)fx << (k + R);
+                this->ry |= (uint32_t)fy << (k + R);
+                this->rz |= (uint32_t)fz << (k + R);
             } else {
                 x[k + R] = wrapc(px + k, d.nx);
                 y[k + R] = wrapc(py + k, d.ny) * d.nx;
@@ -134,7 +151,7 @@ struct Nbr {
             return false;
         } else {
             if (!((par >> AX) & 1)) return false;
-            const uint32_t m = AX == 0 ? rx : (AX == 1 ? ry : rz);
+            const uint32_t m = AX == 0 ? this->rx : (AX == 1 ? this->ry : this->rz);
             return (m >> (k + R)) & 1u;
         }
     }
@@ -195,6 +212,31 @@ __device__ __forceinline__ T D2(const P *__restrict__ f, const Nbr<R, SYM> &nb, 
     return s;
 }
 
+
+// acc + sum_k w_k (f_{+k} - f_{-k}) (w: weights indexed by k = 1..R; a
+// negative sign is folded into the FMA); acc + sum_k w_k (f_{+k} + f_{-k})
+// (the centre tap is the caller's).
+template <int R, int AX, int POL, typename T, typename P, bool SYM>
+__device__ __forceinline__ T add_d1(T acc, const P *__restrict__ f, const Nbr<R, SYM> &nb, const T *w, int par,
+                                    bool negate = false) {
+#pragma unroll
+    for (int k = R; k >= 1; --k) {
+        const T fp = neg_if(nb.template flip<AX>(k, par), ld<POL, T>(f + nb.template at<AX>(k)));
+        const T fm = neg_if(nb.template flip<AX>(-k, par), ld<POL, T>(f + nb.template at<AX>(-k)));
+        acc = fma(negate ? -w[k] : w[k], fp - fm, acc);
+    }
+    return acc;
+}
+template <int R, int AX, int POL, typename T, typename P, bool SYM>
+__device__ __forceinline__ T add_d2(T acc, const P *__restrict__ f, const Nbr<R, SYM> &nb, const T *w, int par) {
+#pragma unroll
+    for (int k = R; k >= 1; --k) {
+        const T fp = neg_if(nb.template flip<AX>(k, par), ld<POL, T>(f + nb.template at<AX>(k)));
+        const T fm = neg_if(nb.template flip<AX>(-k, par), ld<POL, T>(f + nb.template at<AX>(-k)));
+        acc = fma(w[k], fp + fm, acc);
+    }
+    return acc;
+}
 
 // Double-float stencils: differences (sums) of the neighbours are formed with
 // exact head arithmetic and weighted into a compensated accumulator,
@@ -607,54 +649,71 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     const T w = ld<POL, T>(aux + A_W * as + i), div = ld<POL, T>(aux + A_DIV * as + i);
 
     // advective + dilatation half of the skew-symmetric form, per field
+    const T hu = T(-0.5) * u, hv = T(-0.5) * v, hw = T(-0.5) * w, hdiv = T(-0.5) * div;
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
         const S *f = Q + m * qs;
         const int pm = q_parity(m);
         const T dx = D1<R, 0, POL>(f, nb, c, pm), dy = D1<R, 1, POL>(f, nb, c, pm), dz = D1<R, 2, POL>(f, nb, c, pm);
-        T qc = ld<POL, T>(f + i);
-        if constexpr (is_dd<T>) {
-            if (m == 4) qc = qc + a.kdd.e_ref;  // the full rho E multiplies div u
-        }
-        res[m] = T(-0.5) * fma(u, dx, fma(v, dy, fma(w, dz, qc * div)));
+        res[m] = fma(hu, dx, fma(hv, dy, fma(hw, dz, hdiv * ld<POL, T>(f + i))));
         // mass flux d_j(m_j/2): m_j is field 1+j, differentiated along j
         if (m == 1) res[0] = fma(T(-0.5), dx, res[0]);
         if (m == 2) res[0] = fma(T(-0.5), dy, res[0]);
         if (m == 3) res[0] = fma(T(-0.5), dz, res[0]);
     }
-    // momentum fluxes
+    // momentum fluxes -D_j Phi_ij and energy flux -D_j F_j, tap by tap into
+    // the equation's sum
     const T *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
     const T *Pxy = aux + A_PXY * as, *Pxz = aux + A_PXZ * as, *Pyz = aux + A_PYZ * as;
-    res[1] -= D1<R, 0, POL>(Pxx, nb, c) + D1<R, 1, POL>(Pxy, nb, c, PAR_XY) + D1<R, 2, POL>(Pxz, nb, c, PAR_XZ);
-    res[2] -= D1<R, 0, POL>(Pxy, nb, c, PAR_XY) + D1<R, 1, POL>(Pyy, nb, c) + D1<R, 2, POL>(Pyz, nb, c, PAR_YZ);
-    res[3] -= D1<R, 0, POL>(Pxz, nb, c, PAR_XZ) + D1<R, 1, POL>(Pyz, nb, c, PAR_YZ) + D1<R, 2, POL>(Pzz, nb, c);
-    // energy flux
-    res[4] -= D1<R, 0, POL>(aux + A_FX * as, nb, c, PAR_X) + D1<R, 1, POL>(aux + A_FY * as, nb, c, PAR_Y) +
-              D1<R, 2, POL>(aux + A_FZ * as, nb, c, PAR_Z);
-    if constexpr (is_dd<T>) {
-        // F_j = F'_j + (e_ref/2 + p_ref) u_j with F'_j built from the deviations
-        res[4] -= a.kdd.c_ref * div;
-    }
-    // viscous Laplacians: (1/Re)[sum_j L_j u_i + L_i u_i / 3]
-    const T ir = k_inv_re<T>(a), f43 = T(4.0 / 3.0);
+    res[1] = add_d1<R, 0, POL>(res[1], Pxx, nb, c.d1[0], PAR_EVEN, true);
+    res[1] = add_d1<R, 1, POL>(res[1], Pxy, nb, c.d1[1], PAR_XY, true);
+    res[1] = add_d1<R, 2, POL>(res[1], Pxz, nb, c.d1[2], PAR_XZ, true);
+    res[2] = add_d1<R, 0, POL>(res[2], Pxy, nb, c.d1[0], PAR_XY, true);
+    res[2] = add_d1<R, 1, POL>(res[2], Pyy, nb, c.d1[1], PAR_EVEN, true);
+    res[2] = add_d1<R, 2, POL>(res[2], Pyz, nb, c.d1[2], PAR_YZ, true);
+    res[3] = add_d1<R, 0, POL>(res[3], Pxz, nb, c.d1[0], PAR_XZ, true);
+    res[3] = add_d1<R, 1, POL>(res[3], Pyz, nb, c.d1[1], PAR_YZ, true);
+    res[3] = add_d1<R, 2, POL>(res[3], Pzz, nb, c.d1[2], PAR_EVEN, true);
+    res[4] = add_d1<R, 0, POL>(res[4], aux + A_FX * as, nb, c.d1[0], PAR_X, true);
+    res[4] = add_d1<R, 1, POL>(res[4], aux + A_FY * as, nb, c.d1[1], PAR_Y, true);
+    res[4] = add_d1<R, 2, POL>(res[4], aux + A_FZ * as, nb, c.d1[2], PAR_Z, true);
+    // viscous Laplacians (1/Re)[sum_j L_j u_i + L_i u_i / 3] and the heat flux
+    // kappa sum_j L_j T, with 1/Re, 4/(3 Re) and kappa folded into the weights
+    const FoldW<T> &fw = FoldPick<T>::get(a);
     {
-        const T *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as;
-        T vx = ir * fma(f43, D2<R, 0, POL>(Uf, nb, c, PAR_X), D2<R, 1, POL>(Uf, nb, c, PAR_X) + D2<R, 2, POL>(Uf, nb, c, PAR_X));
-        T vy = ir * fma(f43, D2<R, 1, POL>(Vf, nb, c, PAR_Y), D2<R, 0, POL>(Vf, nb, c, PAR_Y) + D2<R, 2, POL>(Vf, nb, c, PAR_Y));
-        T vz = ir * fma(f43, D2<R, 2, POL>(Wf, nb, c, PAR_Z), D2<R, 0, POL>(Wf, nb, c, PAR_Z) + D2<R, 1, POL>(Wf, nb, c, PAR_Z));
+        const T *Uf = aux + A_U * as, *Vf = aux + A_V * as, *Wf = aux + A_W * as, *Tf = aux + A_T * as;
+        T vx = VB ? T(0) : res[1], vy = VB ? T(0) : res[2], vz = VB ? T(0) : res[3];
+        vx = fma(fw.c_u, u, vx);
+        vx = add_d2<R, 0, POL>(vx, Uf, nb, fw.vis43[0], PAR_X);
+        vx = add_d2<R, 1, POL>(vx, Uf, nb, fw.vis[1], PAR_X);
+        vx = add_d2<R, 2, POL>(vx, Uf, nb, fw.vis[2], PAR_X);
+        vy = fma(fw.c_v, v, vy);
+        vy = add_d2<R, 0, POL>(vy, Vf, nb, fw.vis[0], PAR_Y);
+        vy = add_d2<R, 1, POL>(vy, Vf, nb, fw.vis43[1], PAR_Y);
+        vy = add_d2<R, 2, POL>(vy, Vf, nb, fw.vis[2], PAR_Y);
+        vz = fma(fw.c_w, w, vz);
+        vz = add_d2<R, 0, POL>(vz, Wf, nb, fw.vis[0], PAR_Z);
+        vz = add_d2<R, 1, POL>(vz, Wf, nb, fw.vis[1], PAR_Z);
+        vz = add_d2<R, 2, POL>(vz, Wf, nb, fw.vis43[2], PAR_Z);
         if (VB) {
-            // the D_i g_i / 3 part of the viscous momentum term, kept separate
-            const T ir3 = ir * T(1.0 / 3.0);
-            vx = fma(ir3, D1<R, 0, POL>(aux + A_GX * as, nb, c), vx);
-            vy = fma(ir3, D1<R, 1, POL>(aux + A_GY * as, nb, c), vy);
-            vz = fma(ir3, D1<R, 2, POL>(aux + A_GZ * as, nb, c), vz);
+            // form B: the viscous momentum term (with D_i g_i / 3) is also
+            // needed as a value, for the work u_i (viscous term) + tau : grad u
+            vx = add_d1<R, 0, POL>(vx, aux + A_GX * as, nb, fw.g[0], PAR_EVEN);
+            vy = add_d1<R, 1, POL>(vy, aux + A_GY * as, nb, fw.g[1], PAR_EVEN);
+            vz = add_d1<R, 2, POL>(vz, aux + A_GZ * as, nb, fw.g[2], PAR_EVEN);
             res[4] += fma(u, vx, fma(v, vy, fma(w, vz, ld<POL, T>(aux + A_TG * as + i))));
+            res[1] += vx;
+            res[2] += vy;
+            res[3] += vz;
+        } else {
+            res[1] = vx;
+            res[2] = vy;
+            res[3] = vz;
         }
-        res[1] += vx;
-        res[2] += vy;
-        res[3] += vz;
-        const T *Tf = aux + A_T * as;
-        res[4] = fma(k_kappa<T>(a), D2<R, 0, POL>(Tf, nb, c) + D2<R, 1, POL>(Tf, nb, c) + D2<R, 2, POL>(Tf, nb, c), res[4]);
+        res[4] = fma(fw.c_T, ld<POL, T>(Tf + i), res[4]);
+        res[4] = add_d2<R, 0, POL>(res[4], Tf, nb, fw.heat[0], PAR_EVEN);
+        res[4] = add_d2<R, 1, POL>(res[4], Tf, nb, fw.heat[1], PAR_EVEN);
+        res[4] = add_d2<R, 2, POL>(res[4], Tf, nb, fw.heat[2], PAR_EVEN);
     }
     }
 
