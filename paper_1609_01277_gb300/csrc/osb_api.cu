@@ -267,8 +267,10 @@ StageArgs base_args(const osb_grid *g) {
                 f.vis[ax][k] = ir * d2;
                 f.vis43[ax][k] = ir * (4.0 / 3.0) * d2;
                 f.heat[ax][k] = kap * d2;
-                f.g[ax][k] = ir * (1.0 / 3.0) * d1;
+                f.g[ax][k] = (1.0 / 3.0) * d1;
+                f.d1ir[ax][k] = ir * d1;
             }
+        f.Re = g->prm.Re;
         const double d0x = g->c64.d2[0][0], d0y = g->c64.d2[1][0], d0z = g->c64.d2[2][0];
         f.c_u = ir * ((4.0 / 3.0) * d0x + d0y + d0z);
         f.c_v = ir * (d0x + (4.0 / 3.0) * d0y + d0z);
@@ -281,7 +283,9 @@ StageArgs base_args(const osb_grid *g) {
                 h.vis43[ax][k] = (float)f.vis43[ax][k];
                 h.heat[ax][k] = (float)f.heat[ax][k];
                 h.g[ax][k] = (float)f.g[ax][k];
+                h.d1ir[ax][k] = (float)f.d1ir[ax][k];
             }
+        h.Re = (float)f.Re;
         h.c_u = (float)f.c_u;
         h.c_v = (float)f.c_v;
         h.c_w = (float)f.c_w;

@@ -65,12 +65,15 @@ struct Coef {
 
 // Folded weights of the FP64 / FP32 residual: second-derivative weights
 // scaled by 1/Re (vis), 4/(3 Re) (vis43) and kappa (heat), first-derivative
-// weights by 1/(3 Re) (g, viscous form B), and the centre weights of the three
+// weights by 1/3 (g: viscous form B, whose g_i is stored scaled by 1/Re) and
+// by 1/Re (d1ir, the gradient kernel), and the centre weights of the three
 // viscous Laplacians and of the heat-flux Laplacian summed over the axes, so
 // that each equation's terms accumulate with one FMA per stencil tap.
 template <typename T>
 struct FoldW {
     T vis[3][MAXR + 1], vis43[3][MAXR + 1], heat[3][MAXR + 1], g[3][MAXR + 1];
+    T d1ir[3][MAXR + 1];  // first-derivative weights / Re: the gradient kernel forms (1/Re) d_j u_i directly
+    T Re;
     T c_u, c_v, c_w, c_T;  // centre: (1/Re)(4/3 d0_x + d0_y + d0_z), ..., kappa (d0_x + d0_y + d0_z)
 };
 

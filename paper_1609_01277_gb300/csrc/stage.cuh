@@ -378,50 +378,94 @@ __global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
 template <int POL, typename S, int R, bool SYM>
 __device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z);
 
+// Double-float, viscous form B: the gradient, tau, F_j, g_i and tau : grad u
+// in double-float operations (g_i unscaled; the residual's weights for D_i g_i
+// carry 1/(3 Re)).
+template <int POL, typename S, int R, bool SYM>
+__device__ __forceinline__ void grad_point_dd_b(const StageArgs &a, int x, int y, int z) {
+    Nbr<R, SYM> nb;
+    nb.init(x, y, z, a.d);
+    const int i = nb.center();
+    const Coef<dd> &c = a.cdd;
+    dd *aux = static_cast<dd *>(a.aux);
+    const size_t as = a.aux_stride;
+    const dd *U = aux + A_U * as, *V = aux + A_V * as, *W = aux + A_W * as;
+    const dd gxx = D1<R, 0, POL>(U, nb, c, PAR_X), gxy = D1<R, 1, POL>(U, nb, c, PAR_X), gxz = D1<R, 2, POL>(U, nb, c, PAR_X);
+    const dd gyx = D1<R, 0, POL>(V, nb, c, PAR_Y), gyy = D1<R, 1, POL>(V, nb, c, PAR_Y), gyz = D1<R, 2, POL>(V, nb, c, PAR_Y);
+    const dd gzx = D1<R, 0, POL>(W, nb, c, PAR_Z), gzy = D1<R, 1, POL>(W, nb, c, PAR_Z), gzz = D1<R, 2, POL>(W, nb, c, PAR_Z);
+    const dd div = gxx + gyy + gzz;
+    const dd ir = a.kdd.inv_re;
+    const dd tdiv = dd(2.0 / 3.0) * div;
+    const dd txx = ir * (gxx + gxx - tdiv), tyy = ir * (gyy + gyy - tdiv), tzz = ir * (gzz + gzz - tdiv);
+    const dd txy = ir * (gxy + gyx), txz = ir * (gxz + gzx), tyz = ir * (gyz + gzy);
+    const dd u = ld<POL, dd>(aux + A_U * as + i), v = ld<POL, dd>(aux + A_V * as + i);
+    const dd w = ld<POL, dd>(aux + A_W * as + i), p = ld<POL, dd>(aux + A_P * as + i);
+    const S *Q = static_cast<const S *>(a.src);
+    const dd hE = fma(dd(0.5f, 0.f), ld<POL, dd>(Q + 4 * a.src_stride + i), p);
+    aux[A_DIV * as + i] = div;
+    aux[A_FX * as + i] = hE * u;
+    aux[A_FY * as + i] = hE * v;
+    aux[A_FZ * as + i] = hE * w;
+    aux[A_GX * as + i] = gyy + gzz;
+    aux[A_GY * as + i] = gxx + gzz;
+    aux[A_GZ * as + i] = gxx + gyy;
+    aux[A_TG * as + i] = txx * gxx + tyy * gyy + tzz * gzz + txy * (gxy + gyx) + txz * (gxz + gzx) +
+                         tyz * (gyz + gzy);
+}
+
 template <int POL, typename S, typename T, int R, bool VB, bool SYM = false>
 __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int z) {
     if constexpr (is_dd<T> && !VB) {
         grad_point_dd<POL, S, R, SYM>(a, x, y, z);
         return;
+    } else if constexpr (is_dd<T>) {
+        grad_point_dd_b<POL, S, R, SYM>(a, x, y, z);
+        return;
     } else {
     Nbr<R, SYM> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
-    const Coef<T> &c = CoefPick<T>::get(a);
+    const FoldW<T> &fw = FoldPick<T>::get(a);
     T *aux = static_cast<T *>(a.aux);
     const size_t as = a.aux_stride;
     const T *U = aux + A_U * as, *V = aux + A_V * as, *W = aux + A_W * as;
 
-    const T gxx = D1<R, 0, POL>(U, nb, c, PAR_X), gxy = D1<R, 1, POL>(U, nb, c, PAR_X), gxz = D1<R, 2, POL>(U, nb, c, PAR_X);
-    const T gyx = D1<R, 0, POL>(V, nb, c, PAR_Y), gyy = D1<R, 1, POL>(V, nb, c, PAR_Y), gyz = D1<R, 2, POL>(V, nb, c, PAR_Y);
-    const T gzx = D1<R, 0, POL>(W, nb, c, PAR_Z), gzy = D1<R, 1, POL>(W, nb, c, PAR_Z), gzz = D1<R, 2, POL>(W, nb, c, PAR_Z);
-    const T div = gxx + gyy + gzz;
-    const T ir = k_inv_re<T>(a);
-    const T tdiv = T(2.0 / 3.0) * div;
-    const T txx = ir * (gxx + gxx - tdiv), tyy = ir * (gyy + gyy - tdiv), tzz = ir * (gzz + gzz - tdiv);
-    const T txy = ir * (gxy + gyx), txz = ir * (gxz + gzx), tyz = ir * (gyz + gzy);
+    // s_ij = (1/Re) d_j u_i: the 1/Re of tau folded into the stencil weights
+    const T sxx = add_d1<R, 0, POL>(T(0), U, nb, fw.d1ir[0], PAR_X), sxy = add_d1<R, 1, POL>(T(0), U, nb, fw.d1ir[1], PAR_X);
+    const T sxz = add_d1<R, 2, POL>(T(0), U, nb, fw.d1ir[2], PAR_X), syx = add_d1<R, 0, POL>(T(0), V, nb, fw.d1ir[0], PAR_Y);
+    const T syy = add_d1<R, 1, POL>(T(0), V, nb, fw.d1ir[1], PAR_Y), syz = add_d1<R, 2, POL>(T(0), V, nb, fw.d1ir[2], PAR_Y);
+    const T szx = add_d1<R, 0, POL>(T(0), W, nb, fw.d1ir[0], PAR_Z), szy = add_d1<R, 1, POL>(T(0), W, nb, fw.d1ir[1], PAR_Z);
+    const T szz = add_d1<R, 2, POL>(T(0), W, nb, fw.d1ir[2], PAR_Z);
+    const T divs = sxx + syy + szz;  // (1/Re) div u
+    const T tdivs = T(2.0 / 3.0) * divs;
+    // tau_ij = (1/Re)(d_j u_i + d_i u_j - (2/3) div u delta_ij)
+    const T txx = fma(T(2), sxx, -tdivs), tyy = fma(T(2), syy, -tdivs), tzz = fma(T(2), szz, -tdivs);
+    const T txy = sxy + syx, txz = sxz + szx, tyz = syz + szy;
     const T u = ld<POL, T>(aux + A_U * as + i), v = ld<POL, T>(aux + A_V * as + i);
     const T w = ld<POL, T>(aux + A_W * as + i), p = ld<POL, T>(aux + A_P * as + i);
     const S *Q = static_cast<const S *>(a.src);
     const T hE = fma(T(0.5), ld<POL, T>(Q + 4 * a.src_stride + i), p);
-    aux[A_DIV * as + i] = div;
+    aux[A_DIV * as + i] = fw.Re * divs;
     if (!VB) {
         aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
         aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
         aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
-        const T ir3 = ir * T(1.0 / 3.0);
-        aux[A_PXX * as + i] = ld<POL, T>(aux + A_PXX * as + i) - ir3 * (gyy + gzz);
-        aux[A_PYY * as + i] = ld<POL, T>(aux + A_PYY * as + i) - ir3 * (gxx + gzz);
-        aux[A_PZZ * as + i] = ld<POL, T>(aux + A_PZZ * as + i) - ir3 * (gxx + gyy);
+        // Phi_ii - (1/(3 Re)) sum_{k != i} d_k u_k
+        const T third = T(1.0 / 3.0);
+        aux[A_PXX * as + i] = fma(-third, syy + szz, ld<POL, T>(aux + A_PXX * as + i));
+        aux[A_PYY * as + i] = fma(-third, sxx + szz, ld<POL, T>(aux + A_PYY * as + i));
+        aux[A_PZZ * as + i] = fma(-third, sxx + syy, ld<POL, T>(aux + A_PZZ * as + i));
     } else {
         aux[A_FX * as + i] = hE * u;
         aux[A_FY * as + i] = hE * v;
         aux[A_FZ * as + i] = hE * w;
-        aux[A_GX * as + i] = gyy + gzz;
-        aux[A_GY * as + i] = gxx + gzz;
-        aux[A_GZ * as + i] = gxx + gyy;
-        aux[A_TG * as + i] = txx * gxx + tyy * gyy + tzz * gzz + txy * (gxy + gyx) + txz * (gxz + gzx) +
-                             tyz * (gyz + gzy);
+        // g_i scaled by 1/Re (the residual's weights for D_i g_i carry 1/3 only)
+        aux[A_GX * as + i] = syy + szz;
+        aux[A_GY * as + i] = sxx + szz;
+        aux[A_GZ * as + i] = sxx + syy;
+        // tau : grad u = Re sum_ij tau_ij s_ij, with s_ij + s_ji = tau_ij off the diagonal
+        aux[A_TG * as + i] = fw.Re * fma(txx, sxx, fma(tyy, syy, fma(tzz, szz,
+                                         fma(txy, txy, fma(txz, txz, tyz * tyz)))));
     }
     }
 }
@@ -627,6 +671,32 @@ __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R, 
     for (int m = 0; m < 5; ++m) res[m] = acc[m].get();
 }
 
+// One axis of the advective half of the skew-symmetric form (FP64 / FP32):
+// res_m += -(1/2) u_AX D_AX q_m.  The momentum component along AX keeps its
+// derivative, which the mass flux -(1/2) D_AX (rho u_AX) shares; for the other
+// fields, up to radius 3, -(1/2) u_AX is folded into the R weights once and
+// each tap goes straight into the sum (beyond radius 3 the R extra products
+// cost more than the one multiply per field they save).
+template <int R, int AX, int POL, typename S, typename T, bool SYM>
+__device__ __forceinline__ void adv_axis(T (&res)[5], const S *Q, size_t qs, const Nbr<R, SYM> &nb, const Coef<T> &c,
+                                         T vel) {
+    const T hv = T(-0.5) * vel;
+    T wk[R + 1];
+#pragma unroll
+    for (int k = 0; k <= R; ++k) wk[k] = (R <= 3 && k > 0) ? hv * c.d1[AX][k] : T(0);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const S *f = Q + m * qs;
+        if (m == 1 + AX || R > 3) {
+            const T d = D1<R, AX, POL>(f, nb, c, q_parity(m));
+            res[m] = fma(hv, d, res[m]);
+            if (m == 1 + AX) res[0] = fma(T(-0.5), d, res[0]);
+        } else {
+            res[m] = add_d1<R, AX, POL>(res[m], f, nb, wk, q_parity(m));
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_resid: residual and RK update (MODE 0) or residual only (MODE 1)
 // ---------------------------------------------------------------------------
@@ -648,19 +718,14 @@ __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, in
     const T u = ld<POL, T>(aux + A_U * as + i), v = ld<POL, T>(aux + A_V * as + i);
     const T w = ld<POL, T>(aux + A_W * as + i), div = ld<POL, T>(aux + A_DIV * as + i);
 
-    // advective + dilatation half of the skew-symmetric form, per field
-    const T hu = T(-0.5) * u, hv = T(-0.5) * v, hw = T(-0.5) * w, hdiv = T(-0.5) * div;
+    // advective + dilatation half of the skew-symmetric form,
+    // res_m = -(1/2)(q_m div u + u_j D_j q_m), axis by axis
+    const T hdiv = T(-0.5) * div;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        const S *f = Q + m * qs;
-        const int pm = q_parity(m);
-        const T dx = D1<R, 0, POL>(f, nb, c, pm), dy = D1<R, 1, POL>(f, nb, c, pm), dz = D1<R, 2, POL>(f, nb, c, pm);
-        res[m] = fma(hu, dx, fma(hv, dy, fma(hw, dz, hdiv * ld<POL, T>(f + i))));
-        // mass flux d_j(m_j/2): m_j is field 1+j, differentiated along j
-        if (m == 1) res[0] = fma(T(-0.5), dx, res[0]);
-        if (m == 2) res[0] = fma(T(-0.5), dy, res[0]);
-        if (m == 3) res[0] = fma(T(-0.5), dz, res[0]);
-    }
+    for (int m = 0; m < 5; ++m) res[m] = hdiv * ld<POL, T>(Q + m * qs + i);
+    adv_axis<R, 0, POL>(res, Q, qs, nb, c, u);
+    adv_axis<R, 1, POL>(res, Q, qs, nb, c, v);
+    adv_axis<R, 2, POL>(res, Q, qs, nb, c, w);
     // momentum fluxes -D_j Phi_ij and energy flux -D_j F_j, tap by tap into
     // the equation's sum
     const T *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
