@@ -12,7 +12,7 @@
 // queues of 2R+1 values; x/y stencils read the ring, z stencils the queues.
 //
 //   k_zflux: velocity gradient -> energy flux F_j (with the viscous work
-//            u_i tau_ij), g_i = div u - D_i u_i, div u          (7 FP32 fields)
+//            u_i tau_ij), g_i = (div u - D_i u_i)/Re, div u     (7 FP32 fields)
 //   k_zrhs : residual of all equations + RK update, reading Q, F_j, g_i, div u
 //
 // HBM traffic per point and stage (FP32 q, FP64 U): k_zflux reads q (20 B)
@@ -155,6 +155,34 @@ __device__ __forceinline__ float sdy2(const float *p, int ce, const float *c) {
     return s;
 }
 
+// Tap-by-tap accumulation into a sum: acc + sum_k w_k (f_{+k} -+ f_{-k}) along
+// x or y of a shared-memory plane, or along z of a register queue (w indexed
+// by k = 1..R; the centre tap of a second derivative is the caller's).
+template <int R, int STRIDE>
+__device__ __forceinline__ float acc_s1(float acc, const float *p, int ce, const float *w, bool neg = false) {
+#pragma unroll
+    for (int k = R; k >= 1; --k) acc = fmaf(neg ? -w[k] : w[k], p[ce + k * STRIDE] - p[ce - k * STRIDE], acc);
+    return acc;
+}
+template <int R, int STRIDE>
+__device__ __forceinline__ float acc_s2(float acc, const float *p, int ce, const float *w) {
+#pragma unroll
+    for (int k = R; k >= 1; --k) acc = fmaf(w[k], p[ce + k * STRIDE] + p[ce - k * STRIDE], acc);
+    return acc;
+}
+template <int R>
+__device__ __forceinline__ float acc_q1(float acc, const float (&q)[2 * R + 1], const float *w, bool neg = false) {
+#pragma unroll
+    for (int k = R; k >= 1; --k) acc = fmaf(neg ? -w[k] : w[k], q[R + k] - q[R - k], acc);
+    return acc;
+}
+template <int R>
+__device__ __forceinline__ float acc_q2(float acc, const float (&q)[2 * R + 1], const float *w) {
+#pragma unroll
+    for (int k = R; k >= 1; --k) acc = fmaf(w[k], q[R + k] + q[R - k], acc);
+    return acc;
+}
+
 // ---------------------------------------------------------------------------
 // k_zflux
 // ---------------------------------------------------------------------------
@@ -185,7 +213,6 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
     const float *Q = static_cast<const float *>(a.src);
     const size_t qs = a.src_stride, as = a.aux_stride;
     float *aux = static_cast<float *>(a.aux);
-    const Coef<float> &c = a.c32;
     const bool use_tma = tm.use && x0 >= CX && x0 - CX + G::RW <= d.nx && y0 >= R && y0 + TY + R <= d.ny;
     const bool vec16 = (d.nx % 4) == 0;  // 16-byte chunks of a row never straddle the wrap
 
@@ -247,7 +274,8 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
     const int Lbeg = z0 - R, Lend = z1 + R;  // lead planes [Lbeg, Lend)
 #pragma unroll 1
     for (int p = 0; p < PF; ++p) issue(Lbeg + p);
-    const float ir = float(a.ph.inv_re), gm1 = float(a.ph.gm1);
+    const FoldW<float> &fw = a.f32;
+    const float gm1 = float(a.ph.gm1);
 #pragma unroll 1
     for (int L = Lbeg; L < Lend; ++L) {
         wait_plane(L);
@@ -259,7 +287,7 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
         const int sL = ((L % G::NS) + G::NS) % G::NS;
         {
             const float rho = S.ring[sL][0][ce];
-            const float ri = 1.f / rho;
+            const float ri = __fdividef(1.f, rho);
             qpush(qu, S.ring[sL][1][ce] * ri);
             qpush(qv, S.ring[sL][2][ce] * ri);
             qpush(qw, S.ring[sL][3][ce] * ri);
@@ -268,22 +296,23 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
         if (zo < z0) continue;
         const int so = ((zo % G::NS) + G::NS) % G::NS;
         for (int e = tid; e < G::RA; e += NT) {
-            const float ri = 1.f / S.ring[so][0][e];
+            const float ri = __fdividef(1.f, S.ring[so][0][e]);
             S.vel[0][e] = S.ring[so][1][e] * ri;
             S.vel[1][e] = S.ring[so][2][e] * ri;
             S.vel[2][e] = S.ring[so][3][e] * ri;
         }
         __syncthreads();
-        const float gxx = sdx1<R>(S.vel[0], ce, c.d1[0]), gxy = sdy1<R>(S.vel[0], ce, c.d1[1]),
-                    gxz = qd1<R>(qu, c.d1[2]);
-        const float gyx = sdx1<R>(S.vel[1], ce, c.d1[0]), gyy = sdy1<R>(S.vel[1], ce, c.d1[1]),
-                    gyz = qd1<R>(qv, c.d1[2]);
-        const float gzx = sdx1<R>(S.vel[2], ce, c.d1[0]), gzy = sdy1<R>(S.vel[2], ce, c.d1[1]),
-                    gzz = qd1<R>(qw, c.d1[2]);
-        const float div = gxx + gyy + gzz;
-        const float tdiv = (2.f / 3.f) * div;
-        const float txx = ir * (gxx + gxx - tdiv), tyy = ir * (gyy + gyy - tdiv), tzz = ir * (gzz + gzz - tdiv);
-        const float txy = ir * (gxy + gyx), txz = ir * (gxz + gzx), tyz = ir * (gyz + gzy);
+        // s_ij = (1/Re) d_j u_i, the 1/Re of tau folded into the weights
+        const float gxx = sdx1<R>(S.vel[0], ce, fw.d1ir[0]), gxy = sdy1<R>(S.vel[0], ce, fw.d1ir[1]),
+                    gxz = qd1<R>(qu, fw.d1ir[2]);
+        const float gyx = sdx1<R>(S.vel[1], ce, fw.d1ir[0]), gyy = sdy1<R>(S.vel[1], ce, fw.d1ir[1]),
+                    gyz = qd1<R>(qv, fw.d1ir[2]);
+        const float gzx = sdx1<R>(S.vel[2], ce, fw.d1ir[0]), gzy = sdy1<R>(S.vel[2], ce, fw.d1ir[1]),
+                    gzz = qd1<R>(qw, fw.d1ir[2]);
+        const float divs = gxx + gyy + gzz;  // (1/Re) div u
+        const float tdiv = (2.f / 3.f) * divs;
+        const float txx = fmaf(2.f, gxx, -tdiv), tyy = fmaf(2.f, gyy, -tdiv), tzz = fmaf(2.f, gzz, -tdiv);
+        const float txy = gxy + gyx, txz = gxz + gzx, tyz = gyz + gzy;
         const float u = qu[R], v = qv[R], w = qw[R];
         const float rho = S.ring[so][0][ce], e = S.ering[so][tid];
         const float p = gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
@@ -293,10 +322,10 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
             aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
             aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
             aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
-            aux[A_GX * as + i] = gyy + gzz;
+            aux[A_GX * as + i] = gyy + gzz;  // g_i / Re
             aux[A_GY * as + i] = gxx + gzz;
             aux[A_GZ * as + i] = gxx + gyy;
-            aux[A_DIV * as + i] = div;
+            aux[A_DIV * as + i] = fw.Re * divs;
         }
     }
     cp_wait<0>();
@@ -415,8 +444,8 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
         for (int m = 0; m < 5; ++m) qQ[m][k] = 0.f;
         qPxz[k] = qPyz[k] = qPzz[k] = qFz[k] = qU[k] = qV[k] = qW[k] = qT[k] = 0.f;
     }
-    const float ir = float(a.ph.inv_re), ir3 = ir * (1.f / 3.f), gm1 = float(a.ph.gm1),
-                gM2 = float(a.ph.gM2), kap = float(a.ph.kappa), f43 = 4.f / 3.f;
+    // g_i arrive scaled by 1/Re from k_zflux
+    const float third = 1.f / 3.f, gm1 = float(a.ph.gm1), gM2 = float(a.ph.gM2);
     const float bdt = float(a.beta_dt), adt = float(a.alpha_dt);
     float *qo = static_cast<float *>(a.q_out);
     float *cp = static_cast<float *>(a.u32_out);
@@ -436,7 +465,7 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
         {   // lead plane: point-wise quantities of this thread's column
             const float rho = S.ring[sL][RF_RHO][ce], m0 = S.ring[sL][RF_M0][ce], m1 = S.ring[sL][RF_M1][ce],
                         m2 = S.ring[sL][RF_M2][ce], e = S.ring[sL][RF_E][ce];
-            const float ri = 1.f / rho;
+            const float ri = __fdividef(1.f, rho);
             const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
             const float p = gm1 * (e - 0.5f * (m0 * u + m1 * v + m2 * w));
             qpush(qQ[0], rho);
@@ -450,7 +479,7 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
             qpush(qT, gM2 * p * ri);
             qpush(qPxz, 0.5f * m0 * w);
             qpush(qPyz, 0.5f * m1 * w);
-            qpush(qPzz, fmaf(0.5f * m2, w, p) - ir3 * S.cring[sL][1][tid]);
+            qpush(qPzz, fmaf(-third, S.cring[sL][1][tid], fmaf(0.5f * m2, w, p)));
             qpush(qFz, S.cring[sL][0][tid]);
         }
         const int zo = L - R;
@@ -473,44 +502,96 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
         for (int e = tid; e < G::RA; e += NT) {
             const float rho = S.ring[so][RF_RHO][e], m0 = S.ring[so][RF_M0][e], m1 = S.ring[so][RF_M1][e],
                         m2 = S.ring[so][RF_M2][e], en = S.ring[so][RF_E][e];
-            const float ri = 1.f / rho;
+            const float ri = __fdividef(1.f, rho);
             const float u = m0 * ri, v = m1 * ri, w = m2 * ri;
             const float p = gm1 * (en - 0.5f * (m0 * u + m1 * v + m2 * w));
             S.der[DF_U][e] = u;
             S.der[DF_V][e] = v;
             S.der[DF_W][e] = w;
             S.der[DF_T][e] = gM2 * p * ri;
-            S.der[DF_PXX][e] = fmaf(0.5f * m0, u, p) - ir3 * S.ring[so][RF_GX][e];
-            S.der[DF_PYY][e] = fmaf(0.5f * m1, v, p) - ir3 * S.ring[so][RF_GY][e];
+            S.der[DF_PXX][e] = fmaf(-third, S.ring[so][RF_GX][e], fmaf(0.5f * m0, u, p));
+            S.der[DF_PYY][e] = fmaf(-third, S.ring[so][RF_GY][e], fmaf(0.5f * m1, v, p));
             S.der[DF_PXY][e] = 0.5f * m0 * v;
             S.der[DF_PXZ][e] = 0.5f * m0 * w;
             S.der[DF_PYZ][e] = 0.5f * m1 * w;
         }
         __syncthreads();
         const float u = qU[R], v = qV[R], w = qW[R];
+        constexpr int W = G::RW;
         float res[5];
+        // advective half of the skew-symmetric form and dilatation,
+        // res_m = -(1/2)(q_m div u + u_j D_j q_m): -u_j/2 folded into the
+        // weights of axis j (radius <= 3), except for rho u_j along j, whose
+        // derivative the mass flux -(1/2) D_j (rho u_j) shares
+        {
+            const float hdiv = -0.5f * divc, hu = -0.5f * u, hv = -0.5f * v, hw = -0.5f * w;
+            float wx[R + 1], wy[R + 1], wz[R + 1];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            const float *f = S.ring[so][RF_RHO + m];
-            const float dx = sdx1<R>(f, ce, c.d1[0]), dy = sdy1<R>(f, ce, c.d1[1]), dz = qd1<R>(qQ[m], c.d1[2]);
-            res[m] = -0.5f * fmaf(u, dx, fmaf(v, dy, fmaf(w, dz, qQ[m][R] * divc)));
-            if (m == 1) res[0] = fmaf(-0.5f, dx, res[0]);
-            if (m == 2) res[0] = fmaf(-0.5f, dy, res[0]);
-            if (m == 3) res[0] = fmaf(-0.5f, dz, res[0]);
+            for (int k = 1; k <= R; ++k) {
+                wx[k] = hu * c.d1[0][k];
+                wy[k] = hv * c.d1[1][k];
+                wz[k] = hw * c.d1[2][k];
+            }
+#pragma unroll
+            for (int m = 0; m < 5; ++m) res[m] = hdiv * qQ[m][R];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                const float *f = S.ring[so][RF_RHO + m];
+                if (m == 1 || R > 3) {
+                    const float dx = sdx1<R>(f, ce, c.d1[0]);
+                    res[m] = fmaf(hu, dx, res[m]);
+                    if (m == 1) res[0] = fmaf(-0.5f, dx, res[0]);
+                } else {
+                    res[m] = acc_s1<R, 1>(res[m], f, ce, wx);
+                }
+                if (m == 2 || R > 3) {
+                    const float dy = sdy1<R>(f, ce, c.d1[1]);
+                    res[m] = fmaf(hv, dy, res[m]);
+                    if (m == 2) res[0] = fmaf(-0.5f, dy, res[0]);
+                } else {
+                    res[m] = acc_s1<R, W>(res[m], f, ce, wy);
+                }
+                if (m == 3 || R > 3) {
+                    const float dz = qd1<R>(qQ[m], c.d1[2]);
+                    res[m] = fmaf(hw, dz, res[m]);
+                    if (m == 3) res[0] = fmaf(-0.5f, dz, res[0]);
+                } else {
+                    res[m] = acc_q1<R>(res[m], qQ[m], wz);
+                }
+            }
         }
-        res[1] -= sdx1<R>(S.der[DF_PXX], ce, c.d1[0]) + sdy1<R>(S.der[DF_PXY], ce, c.d1[1]) + qd1<R>(qPxz, c.d1[2]);
-        res[2] -= sdx1<R>(S.der[DF_PXY], ce, c.d1[0]) + sdy1<R>(S.der[DF_PYY], ce, c.d1[1]) + qd1<R>(qPyz, c.d1[2]);
-        res[3] -= sdx1<R>(S.der[DF_PXZ], ce, c.d1[0]) + sdy1<R>(S.der[DF_PYZ], ce, c.d1[1]) + qd1<R>(qPzz, c.d1[2]);
-        res[4] -= sdx1<R>(S.ring[so][RF_FX], ce, c.d1[0]) + sdy1<R>(S.ring[so][RF_FY], ce, c.d1[1]) +
-                  qd1<R>(qFz, c.d1[2]);
-        res[1] += ir * fmaf(f43, sdx2<R>(S.der[DF_U], ce, c.d2[0]),
-                            sdy2<R>(S.der[DF_U], ce, c.d2[1]) + qd2<R>(qU, c.d2[2]));
-        res[2] += ir * fmaf(f43, sdy2<R>(S.der[DF_V], ce, c.d2[1]),
-                            sdx2<R>(S.der[DF_V], ce, c.d2[0]) + qd2<R>(qV, c.d2[2]));
-        res[3] += ir * fmaf(f43, qd2<R>(qW, c.d2[2]),
-                            sdx2<R>(S.der[DF_W], ce, c.d2[0]) + sdy2<R>(S.der[DF_W], ce, c.d2[1]));
-        res[4] = fmaf(kap, sdx2<R>(S.der[DF_T], ce, c.d2[0]) + sdy2<R>(S.der[DF_T], ce, c.d2[1]) +
-                               qd2<R>(qT, c.d2[2]), res[4]);
+        // momentum and energy flux divergences, tap by tap
+        res[1] = acc_s1<R, 1>(res[1], S.der[DF_PXX], ce, c.d1[0], true);
+        res[1] = acc_s1<R, W>(res[1], S.der[DF_PXY], ce, c.d1[1], true);
+        res[1] = acc_q1<R>(res[1], qPxz, c.d1[2], true);
+        res[2] = acc_s1<R, 1>(res[2], S.der[DF_PXY], ce, c.d1[0], true);
+        res[2] = acc_s1<R, W>(res[2], S.der[DF_PYY], ce, c.d1[1], true);
+        res[2] = acc_q1<R>(res[2], qPyz, c.d1[2], true);
+        res[3] = acc_s1<R, 1>(res[3], S.der[DF_PXZ], ce, c.d1[0], true);
+        res[3] = acc_s1<R, W>(res[3], S.der[DF_PYZ], ce, c.d1[1], true);
+        res[3] = acc_q1<R>(res[3], qPzz, c.d1[2], true);
+        res[4] = acc_s1<R, 1>(res[4], S.ring[so][RF_FX], ce, c.d1[0], true);
+        res[4] = acc_s1<R, W>(res[4], S.ring[so][RF_FY], ce, c.d1[1], true);
+        res[4] = acc_q1<R>(res[4], qFz, c.d1[2], true);
+        // viscous Laplacians and heat flux with 1/Re, 4/(3 Re), kappa folded
+        // into the weights and one centre weight per equation
+        const FoldW<float> &fw = a.f32;
+        res[1] = fmaf(fw.c_u, u, res[1]);
+        res[1] = acc_s2<R, 1>(res[1], S.der[DF_U], ce, fw.vis43[0]);
+        res[1] = acc_s2<R, W>(res[1], S.der[DF_U], ce, fw.vis[1]);
+        res[1] = acc_q2<R>(res[1], qU, fw.vis[2]);
+        res[2] = fmaf(fw.c_v, v, res[2]);
+        res[2] = acc_s2<R, 1>(res[2], S.der[DF_V], ce, fw.vis[0]);
+        res[2] = acc_s2<R, W>(res[2], S.der[DF_V], ce, fw.vis43[1]);
+        res[2] = acc_q2<R>(res[2], qV, fw.vis[2]);
+        res[3] = fmaf(fw.c_w, w, res[3]);
+        res[3] = acc_s2<R, 1>(res[3], S.der[DF_W], ce, fw.vis[0]);
+        res[3] = acc_s2<R, W>(res[3], S.der[DF_W], ce, fw.vis[1]);
+        res[3] = acc_q2<R>(res[3], qW, fw.vis43[2]);
+        res[4] = fmaf(fw.c_T, qT[R], res[4]);
+        res[4] = acc_s2<R, 1>(res[4], S.der[DF_T], ce, fw.heat[0]);
+        res[4] = acc_s2<R, W>(res[4], S.der[DF_T], ce, fw.heat[1]);
+        res[4] = acc_q2<R>(res[4], qT, fw.heat[2]);
         if (a.closure) {
 #pragma unroll
             for (int m = 0; m < 5; ++m) res[m] += a.closure[(size_t)m * d.n + i];
