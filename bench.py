@@ -86,7 +86,7 @@ ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}  # fused minimum per poin
 # name bench.py reports.
 TRAFFIC_PER_LAUNCH = {
     ("tgv_256^3_order4_fp64", "k_resid"): 4.6204e9,  # profiles/launches_tgv256_o4_fp64.md
-    ("tgv_256^3_order4_fp32", "k_zrhs"): 2.4776e9,   # profiles/launches_tgv256_o4_fp32.md
+    ("tgv_256^3_order4_fp32", "k_zrhs"): 2.4778e9,   # profiles/launches_tgv256_o4_fp32.md
 }
 
 # FP64 peak from unit counts and clocks: 2 DFMA thread-instructions per SM per
