@@ -502,6 +502,16 @@ def run_ours(args):
         del gE
         variants["euler_order4_fp64"] = {"value": args.steps * npts / (msE * 1e-3), "ms_per_step": msE / args.steps,
                                          "stages_per_step": 1}
+        # kinetic energy and enstrophy of every step, fused into the first stage
+        for prec in ("fp64", "fp32"):
+            gD = make_grid(osb, w, 4, prec, noise_dev)
+            gD.set_diag_series(args.steps + args.warmup)
+            msD, _ = time_steps(torch, gD, args.steps, args.warmup)
+            del gD
+            base = variants.get(f"order4_{prec}", {}).get("ms_per_step")
+            variants[f"order4_{prec}_with_diag_series"] = {
+                "value": args.steps * 3 * npts / (msD * 1e-3), "ms_per_step": msD / args.steps,
+                "overhead_vs_plain": (msD / args.steps) / base - 1.0 if base else None}
         # the Taylor-Green vortex of the full 2 pi box computed on one octant
         # between its symmetry planes: (n/2)^3 points, mirrored stencil loads
         h = n // 2

@@ -114,6 +114,27 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *params,
 /* Frees the host metadata of a grid; never touches the caller's buffers. */
 osb_status osb_grid_destroy(osb_grid *grid);
 
+/* Per-step diagnostics series (Section 3.3 grid means), fused into the first
+ * RK stage: with a series attached, every osb_rk3_step / osb_euler_step step
+ * appends the kinetic energy <(1/2) rho u.u> and the enstrophy
+ * <(1/2) rho |omega|^2> (omega_i = eps_ijk d_j u_k, first-derivative stencil)
+ * of the state at the START of the step, i.e. the step's stencil source.  The
+ * stage kernel that forms the velocity gradient sums both over its thread
+ * blocks (warp shuffles, FP64 block sums); one small kernel adds the block
+ * sums in a fixed order, so the values are deterministic.  The FP64 and
+ * double-float paths equal osb_diagnostics' ke and enstrophy up to rounding;
+ * the FP32 path evaluates them from its FP32 stencil source (relative
+ * error ~1e-7).
+ *  series_dev: device FP64 ring of 2*capacity values, caller-owned: entry k
+ *    (the k-th step after this call) goes to series_dev[2 (k mod capacity)],
+ *    ke first.  NULL detaches.  Resets the step counter to 0.
+ * osb_diag_series_count returns the number of steps recorded (synchronises
+ * the stream).  osb_batch_step refuses grids with a series
+ * (OSB_ERR_UNSUPPORTED).  Errors: OSB_ERR_INVALID_ARG (capacity < 1, or a
+ * buffer not 8-byte aligned). */
+osb_status osb_set_diag_series(osb_grid *grid, double *series_dev, int capacity);
+osb_status osb_diag_series_count(osb_grid *grid, long long *count);
+
 /* Boundary conditions per axis (Section 2.6, "Boundary conditions").
  *  OSB_BC_PERIODIC (every axis after osb_grid_create): the axis is [0, 2 pi),
  *    points x_i = 2 pi i / n, halos wrap around.

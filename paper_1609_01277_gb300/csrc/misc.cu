@@ -87,6 +87,52 @@ cudaError_t launch_to_f32(const double *U, size_t u_stride, float *q, size_t q_s
 }
 
 // ---------------------------------------------------------------------------
+// Per-step diagnostics series: one block sums the first stage's block records
+// in index order (fixed per thread, then a fixed-order combine), divides by
+// the number of points and appends the two means to the ring `series`.
+// ---------------------------------------------------------------------------
+constexpr int SERIES_THREADS = 256;
+
+__global__ void __launch_bounds__(SERIES_THREADS)
+    k_series_final(const double *__restrict__ rec, double inv_n, double *__restrict__ series, int capacity,
+                   int *__restrict__ count) {
+    const long long nrec = (long long)rec[0];
+    double a = 0.0, b = 0.0;
+    for (long long r = threadIdx.x; r < nrec; r += SERIES_THREADS) {
+        a += rec[2 + 2 * r];
+        b += rec[3 + 2 * r];
+    }
+    __shared__ double part[2][SERIES_THREADS];
+    part[0][threadIdx.x] = a;
+    part[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int h = SERIES_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            part[0][threadIdx.x] += part[0][threadIdx.x + h];
+            part[1][threadIdx.x] += part[1][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const int k = *count;
+        const int slot = k % capacity;
+        series[2 * slot] = part[0][0] * inv_n;
+        series[2 * slot + 1] = part[1][0] * inv_n;
+        *count = k + 1;
+    }
+}
+
+cudaError_t launch_series_final(const double *rec, double inv_n, double *series, int capacity, int *count,
+                                cudaStream_t st) {
+    k_series_final<<<1, SERIES_THREADS, 0, st>>>(rec, inv_n, series, capacity, count);
+    return cudaGetLastError();
+}
+
+long long series_max_records(const Dims &d) {
+    return (long long)((d.nx + BX - 1) / BX) * ((d.ny + BY - 1) / BY) * d.nz;
+}
+
+// ---------------------------------------------------------------------------
 // Diagnostics (Section 3.3): grid sums of (1/2) rho u_j u_j, (1/2) rho |omega|^2
 // with omega_i = eps_ijk D_j u_k, the conserved fields, the non-finite count
 // and the max of dt sum_j (|u_j| + c)/h_j.  FP64 from the FP64 accumulator.

@@ -57,6 +57,12 @@ struct osb_grid {
     zm::ZTma *ztma;           // [2 sources][flux, rhs]
     int *kerr;                // device error word of bounded in-kernel waits
     cudaGraphExec_t step_graph[2];  // one RK3 step starting with Q^n in U[0] / U[1]
+    // per-step diagnostics series (osb_set_diag_series): block records of the
+    // first stage (workspace), the caller's ring and its device step counter
+    double *diag_rec;
+    double *series;
+    int series_cap;
+    int *series_count;
 };
 
 namespace {
@@ -108,6 +114,14 @@ size_t diag_bytes(const osb_grid_desc *d) {
     Dims dd{d->nx, d->ny, d->nz, (int)npoints(d)};
     return round256((size_t)(diag_num_partials(dd) + 1) * DIAG_STRIDE * sizeof(double));
 }
+
+// First-stage block records of the diagnostics series, then its step counter.
+size_t series_bytes(const osb_grid_desc *d) {
+    Dims dd{d->nx, d->ny, d->nz, (int)npoints(d)};
+    return round256((size_t)(2 + 2 * series_max_records(dd)) * sizeof(double)) + 256;
+}
+
+size_t workspace_bytes(const osb_grid_desc *d) { return aux_bytes(d) + diag_bytes(d) + batch_bytes() + series_bytes(d); }
 
 // Central-difference weights of order 2r (closed form): first derivative
 // c_k = (-1)^{k+1} (r!)^2 / (k (r-k)! (r+k)!), second derivative d_k = 2 c_k / k,
@@ -372,7 +386,7 @@ const char *osb_last_error(void) { return g_err.c_str(); }
 size_t osb_state_bytes(const osb_grid_desc *d) { return desc_ok(d) ? state_bytes(d) : 0; }
 
 size_t osb_workspace_bytes(const osb_grid_desc *d) {
-    return desc_ok(d) ? aux_bytes(d) + diag_bytes(d) + batch_bytes() : 0;
+    return desc_ok(d) ? workspace_bytes(d) : 0;
 }
 
 osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, void *state_dev, size_t state_len,
@@ -388,7 +402,7 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     if (((uintptr_t)state_dev & 255) || ((uintptr_t)ws_dev & 255))
         return fail(OSB_ERR_BUFFER, "device buffers must be 256-byte aligned");
     if (state_len < state_bytes(desc)) return fail(OSB_ERR_BUFFER, "state buffer too small");
-    if (ws_len < aux_bytes(desc) + diag_bytes(desc) + batch_bytes()) return fail(OSB_ERR_BUFFER, "workspace too small");
+    if (ws_len < workspace_bytes(desc)) return fail(OSB_ERR_BUFFER, "workspace too small");
 
     osb_grid *g = new (std::nothrow) osb_grid;
     if (!g) return fail(OSB_ERR_INVALID_ARG, "host allocation failed");
@@ -420,6 +434,8 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
     g->batch_rec = (BatchInst *)(g->ws + aux_bytes(desc) + diag_bytes(desc));
     g->batch_ctl = (char *)g->batch_rec + round256(sizeof(BatchInst));
     g->kerr = (int *)(g->batch_ctl + BATCH_CTL_BYTES - sizeof(int));
+    g->diag_rec = (double *)(g->ws + aux_bytes(desc) + diag_bytes(desc) + batch_bytes());
+    g->series_count = (int *)((char *)g->diag_rec + series_bytes(desc) - 256);
     if (cudaMemsetAsync(g->kerr, 0, sizeof(int), g->st) != cudaSuccess) {
         delete g;
         return cuda_fail(cudaErrorInvalidValue, "grid create: error word reset");
@@ -635,6 +651,7 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     a.alpha_dt = RK_ALPHA[k] * g->prm.dt;
     a.beta_dt = RK_BETA[k] * g->prm.dt;
     a.ev = nullptr;
+    a.diag_rec = (k == 0 && g->series) ? g->diag_rec : nullptr;
     if (f32 && g->ztma) {
         const int b = (a.src == g->q[0]) ? 0 : 1;
         a.ztma_flux = &g->ztma[2 * b];
@@ -654,6 +671,12 @@ static osb_status ensure_stage_copy(osb_grid *g) {
     return OSB_OK;
 }
 
+// After a first stage with diagnostics: append the step's two means.
+static cudaError_t series_append(const osb_grid *g, cudaStream_t st) {
+    if (!g->series) return cudaSuccess;
+    return launch_series_final(g->diag_rec, 1.0 / (double)g->d.n, g->series, g->series_cap, g->series_count, st);
+}
+
 static osb_status rk3_one_step(osb_grid *g) {
     osb_status s0 = ensure_stage_copy(g);
     if (s0 != OSB_OK) return s0;
@@ -669,6 +692,7 @@ static osb_status rk3_one_step(osb_grid *g) {
         }
         cudaError_t e = g->K.stage(a);
         if (e != cudaSuccess) return cuda_fail(e, "rk3 stage launch");
+        if (k == 0 && (e = series_append(g, g->st)) != cudaSuccess) return cuda_fail(e, "series launch");
     }
     g->cur = 1 - g->cur;
     g->qc = g->cur;
@@ -701,6 +725,7 @@ static osb_status step_graph(osb_grid *g, int cur, cudaGraphExec_t *out) {
         StageArgs a = stage_args(g, cur, k);
         a.stream = g->capture_st;
         el = g->K.stage(a);
+        if (k == 0 && el == cudaSuccess) el = series_append(g, g->capture_st);
     }
     e = cudaStreamEndCapture(g->capture_st, &graph);
     if (el != cudaSuccess || e != cudaSuccess) {
@@ -762,6 +787,7 @@ osb_status osb_euler_step(osb_grid *g, int nsteps) {
         }
         cudaError_t e = g->K.stage(a);
         if (e != cudaSuccess) return cuda_fail(e, "euler stage launch");
+        if ((e = series_append(g, g->st)) != cudaSuccess) return cuda_fail(e, "series launch");
         g->cur = 1 - g->cur;
         g->qc = g->cur;
         g->step += 1;
@@ -859,6 +885,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
         if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
         if (grids[i]->closure) return fail(OSB_ERR_UNSUPPORTED, "batch: grids with a learned closure step singly");
         if (grids[i]->d.sym) return fail(OSB_ERR_UNSUPPORTED, "batch: grids with symmetry boundaries step singly");
+        if (grids[i]->series) return fail(OSB_ERR_UNSUPPORTED, "batch: grids recording a diagnostics series step singly");
     }
     const osb_grid *g0 = grids[0];
     for (int i = 1; i < n; ++i) {
@@ -898,6 +925,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
             for (int k = 0; k < 3; ++k) {
                 rec.st[par][k] = stage_args(g, par, k);
                 rec.st[par][k].ztma_flux = rec.st[par][k].ztma_rhs = nullptr;  // host pointers: not used on the device
+                rec.st[par][k].diag_rec = nullptr;
                 rec.zsrc[par][k] = (rec.st[par][k].src == g->q[0]) ? 0 : 1;
             }
         rec.tz = tile_depth(g->desc);
@@ -1010,6 +1038,35 @@ osb_status osb_grid_set_closure(osb_grid *g, osb_closure *c) {
     if (c && g->desc.precision == OSB_DF64) return fail(OSB_ERR_UNSUPPORTED, "closures take FP64 or FP32 grids");
     if (c && g->d.sym) return fail(OSB_ERR_UNSUPPORTED, "closures take periodic grids");
     g->closure = c;
+    return OSB_OK;
+}
+
+// Per-step diagnostics series (Section 3.3 kinetic energy and enstrophy of
+// the state at the start of every step), fused into the first stage.
+osb_status osb_set_diag_series(osb_grid *g, double *series_dev, int capacity) {
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    if (series_dev && (capacity < 1 || ((uintptr_t)series_dev & 7)))
+        return fail(OSB_ERR_INVALID_ARG, "series: capacity >= 1 and an 8-byte aligned buffer");
+    // captured step graphs hold the previous first-stage arguments
+    for (int b = 0; b < 2; ++b)
+        if (g->step_graph[b]) {
+            cudaGraphExecDestroy(g->step_graph[b]);
+            g->step_graph[b] = nullptr;
+        }
+    g->series = series_dev;
+    g->series_cap = series_dev ? capacity : 0;
+    cudaError_t e = cudaMemsetAsync(g->series_count, 0, sizeof(int), g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "series counter reset");
+    return OSB_OK;
+}
+
+osb_status osb_diag_series_count(osb_grid *g, long long *count) {
+    if (!g || !count) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, g->series_count, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return cuda_fail(e, "series count");
+    *count = h;
     return OSB_OK;
 }
 

@@ -122,6 +122,11 @@ struct StageArgs {
     const void *ztma_flux;  // host: TMA descriptors of the z-march kernels for this stage, or nullptr
     const void *ztma_rhs;
     int *kerr;              // device word set when a bounded in-kernel wait ran out
+    // per-step diagnostics fused into the first stage (or nullptr): the
+    // gradient kernel adds (1/2) rho u.u and (1/2) rho |omega|^2 over each
+    // block; layout: [0] = number of block records, [2 + 2b], [3 + 2b] = the
+    // two sums of block b
+    double *diag_rec;
 };
 
 
@@ -210,5 +215,11 @@ int diag_num_partials(const Dims &d);
 cudaError_t launch_to_dd(const double *U, size_t u_stride, dd *q, size_t q_stride, int n, double e_ref,
                          cudaStream_t st);
 cudaError_t launch_to_f32(const double *U, size_t u_stride, float *q, size_t q_stride, int n, cudaStream_t st);
+// Per-step diagnostics series: sums the block records of the first stage and
+// writes the two grid means into series[2 (count mod capacity)], then counts.
+cudaError_t launch_series_final(const double *rec, double inv_n, double *series, int capacity, int *count,
+                                cudaStream_t st);
+// Upper bound on the block records of one first stage (the gradient kernel's grid).
+long long series_max_records(const Dims &d);
 
 }  // namespace osb

@@ -328,6 +328,37 @@ __host__ __device__ __forceinline__ float d2f_bits(double d) {
     return bitsf(r);
 }
 
+// Sums (a, b) over the thread block in a fixed order -- warp shuffles, then
+// thread 0 over the per-warp sums -- and writes the block's record of the
+// first-stage diagnostics (layout at StageArgs::diag_rec).  Every thread of
+// the block must call it.
+__device__ __forceinline__ void block_record2(double a, double b, double *rec) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    __shared__ double part[2][32];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nw = (blockDim.x * blockDim.y * blockDim.z + 31) >> 5;
+    if ((tid & 31) == 0) {
+        part[0][tid >> 5] = a;
+        part[1][tid >> 5] = b;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double s0 = 0.0, s1 = 0.0;
+        for (int w = 0; w < nw; ++w) {
+            s0 += part[0][w];
+            s1 += part[1][w];
+        }
+        const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        rec[2 + 2 * blk] = s0;
+        rec[3 + 2 * blk] = s1;
+        if (blk == 0) rec[0] = (double)gridDim.x * gridDim.y * gridDim.z;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_prim: primitives and the point-wise momentum fluxes
 // ---------------------------------------------------------------------------
@@ -376,13 +407,23 @@ __global__ void __launch_bounds__(BX *BY) k_prim(const StageArgs a) {
 // k_grad: velocity gradient -> div u, tau_ij, energy flux, viscous g-term
 // ---------------------------------------------------------------------------
 template <int POL, typename S, int R, bool SYM>
-__device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z);
+__device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z, double *dg);
 
 // Double-float, viscous form B: the gradient, tau, F_j, g_i and tau : grad u
 // in double-float operations (g_i unscaled; the residual's weights for D_i g_i
 // carry 1/(3 Re)).
+// (1/2) rho u.u and (1/2) rho |omega|^2 at a point (Section 3.3), from
+// double-float values, in FP64
+__device__ __forceinline__ void point_diag_dd(double *dg, const dd &rho, const dd &u, const dd &v, const dd &w,
+                                              const dd &w0, const dd &w1, const dd &w2) {
+    const double r = double(rho), uu = double(u), vv = double(v), ww = double(w);
+    const double o0 = double(w0), o1 = double(w1), o2 = double(w2);
+    dg[0] = 0.5 * r * (uu * uu + vv * vv + ww * ww);
+    dg[1] = 0.5 * r * (o0 * o0 + o1 * o1 + o2 * o2);
+}
+
 template <int POL, typename S, int R, bool SYM>
-__device__ __forceinline__ void grad_point_dd_b(const StageArgs &a, int x, int y, int z) {
+__device__ __forceinline__ void grad_point_dd_b(const StageArgs &a, int x, int y, int z, double *dg) {
     Nbr<R, SYM> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
@@ -411,15 +452,18 @@ __device__ __forceinline__ void grad_point_dd_b(const StageArgs &a, int x, int y
     aux[A_GZ * as + i] = gxx + gyy;
     aux[A_TG * as + i] = txx * gxx + tyy * gyy + tzz * gzz + txy * (gxy + gyx) + txz * (gxz + gzx) +
                          tyz * (gyz + gzy);
+    if (dg) point_diag_dd(dg, ld<POL, dd>(Q + i), u, v, w, gzy - gyz, gxz - gzx, gyx - gxy);
 }
 
+// dg (or nullptr): receives (1/2) rho u.u and (1/2) rho |omega|^2 of the point,
+// omega_i = eps_ijk D_j u_k, for the first-stage diagnostics.
 template <int POL, typename S, typename T, int R, bool VB, bool SYM = false>
-__device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int z) {
+__device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int z, double *dg = nullptr) {
     if constexpr (is_dd<T> && !VB) {
-        grad_point_dd<POL, S, R, SYM>(a, x, y, z);
+        grad_point_dd<POL, S, R, SYM>(a, x, y, z, dg);
         return;
     } else if constexpr (is_dd<T>) {
-        grad_point_dd_b<POL, S, R, SYM>(a, x, y, z);
+        grad_point_dd_b<POL, S, R, SYM>(a, x, y, z, dg);
         return;
     } else {
     Nbr<R, SYM> nb;
@@ -467,6 +511,14 @@ __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int
         aux[A_TG * as + i] = fw.Re * fma(txx, sxx, fma(tyy, syy, fma(tzz, szz,
                                          fma(txy, txy, fma(txz, txz, tyz * tyz)))));
     }
+    if (dg) {
+        // omega = Re (s_zy - s_yz, s_xz - s_zx, s_yx - s_xy)
+        const T rho = ld<POL, T>(Q + i);
+        const T o0 = szy - syz, o1 = sxz - szx, o2 = syx - sxy;
+        const double Re = double(fw.Re);
+        dg[0] = double(T(0.5) * rho * fma(u, u, fma(v, v, w * w)));
+        dg[1] = double(T(0.5) * rho * fma(o0, o0, fma(o1, o1, o2 * o2))) * (Re * Re);
+    }
     }
 }
 
@@ -477,7 +529,7 @@ __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int
 __device__ __forceinline__ void acc_add(dd_acc &acc, const dd &w, const dd &x) { acc.add_prod(w, x.hi, x.lo); }
 
 template <int POL, typename S, int R, bool SYM>
-__device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z) {
+__device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z, double *dg) {
     Nbr<R, SYM> nb;
     nb.init(x, y, z, a.d);
     const int i = nb.center();
@@ -544,13 +596,20 @@ __device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, 
     aux[A_PXX * as + i] = px.get();
     aux[A_PYY * as + i] = py.get();
     aux[A_PZZ * as + i] = pz.get();
+    if (dg) point_diag_dd(dg, ld<POL, dd>(Q + i), u, v, w, gzy - gyz, gxz - gzx, gyx - gxy);
 }
 
 template <typename S, typename T, int R, bool VB, bool SYM>
 __global__ void __launch_bounds__(BX *BY) k_grad(const StageArgs a) {
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
-    if (x >= a.d.nx || y >= a.d.ny) return;
-    grad_point<LD_NC, S, T, R, VB, SYM>(a, x, y, z);
+    if (!a.diag_rec) {
+        if (x >= a.d.nx || y >= a.d.ny) return;
+        grad_point<LD_NC, S, T, R, VB, SYM>(a, x, y, z);
+        return;
+    }
+    double dg[2] = {0.0, 0.0};
+    if (x < a.d.nx && y < a.d.ny) grad_point<LD_NC, S, T, R, VB, SYM>(a, x, y, z, dg);
+    block_record2(dg[0], dg[1], a.diag_rec);
 }
 
 // ---------------------------------------------------------------------------

@@ -201,7 +201,8 @@ struct FluxSmem {
 // launch is read through L2 only (TMA, 16-byte cp.async.cg, ld.global.cg).
 // bars: the NS ring-slot mbarriers (initialised by the caller); phase: their
 // parity bits, carried across calls.
-template <int R, bool PERSIST>
+// DIAG: also sum the first-stage diagnostics into the block's record.
+template <int R, bool PERSIST, bool DIAG = false>
 __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, int x0, int y0, int z0, int z1,
                                            FluxSmem<R> &S, unsigned long long *bars, uint32_t &phase) {
     using G = Geo<R>;
@@ -275,6 +276,9 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
 #pragma unroll 1
     for (int p = 0; p < PF; ++p) issue(Lbeg + p);
     const FoldW<float> &fw = a.f32;
+    // first-stage diagnostics: this thread's sums of (1/2) rho u.u and
+    // (1/2) rho |omega|^2 over its column, in FP64
+    double dg_ke = 0.0, dg_ens = 0.0;
     const float gm1 = float(a.ph.gm1);
 #pragma unroll 1
     for (int L = Lbeg; L < Lend; ++L) {
@@ -317,6 +321,11 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
         const float rho = S.ring[so][0][ce], e = S.ering[so][tid];
         const float p = gm1 * (e - 0.5f * rho * (u * u + v * v + w * w));
         const float hE = fmaf(0.5f, e, p);
+        if (DIAG && active) {
+            const float o0 = gzy - gyz, o1 = gxz - gzx, o2 = gyx - gxy;  // omega / Re
+            dg_ke += double(0.5f * rho * fmaf(u, u, fmaf(v, v, w * w)));
+            dg_ens += double(0.5f * rho * fmaf(o0, o0, fmaf(o1, o1, o2 * o2)));
+        }
         if (active) {
             const size_t i = (size_t)zo * plane + coff;
             aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
@@ -330,9 +339,13 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
     }
     cp_wait<0>();
     __syncthreads();  // the ring may be refilled by the caller's next tile
+    if constexpr (DIAG) {
+        const double Re = double(fw.Re);
+        block_record2(dg_ke, dg_ens * (Re * Re), a.diag_rec);
+    }
 }
 
-template <int R>
+template <int R, bool DIAG>
 __global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, const __grid_constant__ ZTma tm) {
     using G = Geo<R>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -343,7 +356,8 @@ __global__ void __launch_bounds__(NT, 2) k_zflux(const StageArgs a, int zchunk, 
     }
     uint32_t phase = 0;
     const int z0 = blockIdx.z * zchunk;
-    zflux_body<R, false>(a, tm, blockIdx.x * TX, blockIdx.y * TY, z0, min(z0 + zchunk, a.d.nz), S, S.bars, phase);
+    zflux_body<R, false, DIAG>(a, tm, blockIdx.x * TX, blockIdx.y * TY, z0, min(z0 + zchunk, a.d.nz), S, S.bars,
+                               phase);
 }
 
 // ---------------------------------------------------------------------------
@@ -658,7 +672,8 @@ cudaError_t launch_zstage(const StageArgs &a) {
     zchunk = zchunk < 4 ? 4 : (zchunk > 32 ? 32 : zchunk);
     dim3 grd((a.d.nx + TX - 1) / TX, (a.d.ny + TY - 1) / TY, (a.d.nz + zchunk - 1) / zchunk);
     const size_t sf = flux_smem<R>(), sr = rhs_smem<R>();
-    cudaError_t e = cudaFuncSetAttribute(k_zflux<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
+    auto kflux = a.diag_rec ? k_zflux<R, true> : k_zflux<R, false>;
+    cudaError_t e = cudaFuncSetAttribute(kflux, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sf);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_zrhs<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sr);
     if (e != cudaSuccess) return e;
@@ -667,7 +682,7 @@ cudaError_t launch_zstage(const StageArgs &a) {
     const ZTma &tr = a.ztma_rhs ? *static_cast<const ZTma *>(a.ztma_rhs) : none;
     if (a.ev) cudaEventRecord(a.ev[0], a.stream);
     if (a.ev) cudaEventRecord(a.ev[1], a.stream);  // no separate primitive kernel
-    k_zflux<R><<<grd, NT, sf, a.stream>>>(a, zchunk, tf);
+    kflux<<<grd, NT, sf, a.stream>>>(a, zchunk, tf);
     if (a.ev) cudaEventRecord(a.ev[2], a.stream);
     k_zrhs<R><<<grd, NT, sr, a.stream>>>(a, zchunk, tr);
     if (a.ev) cudaEventRecord(a.ev[3], a.stream);

@@ -33,7 +33,8 @@ EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_gri
            "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_closure_create", "osb_closure_destroy",
            "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_set_dissipative", "osb_closure_set_loss_weight", "osb_closure_status", "osb_closure_sync_weights",
            "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
-           "osb_box_filter", "osb_scalar_rk3", "osb_set_boundaries", "osb_profile_start", "osb_profile_stop",
+           "osb_box_filter", "osb_scalar_rk3", "osb_set_boundaries", "osb_set_diag_series",
+           "osb_diag_series_count", "osb_profile_start", "osb_profile_stop",
            "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
@@ -96,6 +97,8 @@ def load(path: str | None = None):
     L.osb_scalar_rk3.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
     L.osb_set_boundaries.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.osb_set_diag_series.argtypes = [vp, vp, ctypes.c_int]
+    L.osb_diag_series_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.osb_profile_start.argtypes = [vp, ctypes.c_int]
     L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.osb_status_string.argtypes = [ctypes.c_int]
@@ -235,6 +238,31 @@ class Grid:
     def euler_step(self, nsteps: int = 1) -> None:
         """Forward Euler steps (Section 2.4), mixable with step()."""
         check(load().osb_euler_step(self.handle, int(nsteps)), "osb_euler_step")
+
+    def set_diag_series(self, capacity: int | None) -> None:
+        """Record the kinetic energy and enstrophy of the state at the start of
+        every step (fused into the first stage) into a device ring of
+        ``capacity`` entries; None stops recording."""
+        torch = self._torch
+        if capacity is None:
+            check(load().osb_set_diag_series(self.handle, None, 0), "osb_set_diag_series")
+            self._series = None
+            return
+        self._series = torch.zeros(2 * int(capacity), dtype=torch.float64, device=self.state.device)
+        check(load().osb_set_diag_series(self.handle, self._series.data_ptr(), int(capacity)), "osb_set_diag_series")
+
+    def diag_series(self) -> np.ndarray:
+        """(steps, 2) array of (ke, enstrophy), oldest first (the last
+        ``capacity`` steps once the ring has wrapped)."""
+        n = ctypes.c_longlong()
+        check(load().osb_diag_series_count(self.handle, ctypes.byref(n)), "osb_diag_series_count")
+        buf = self._series.cpu().numpy().reshape(-1, 2)
+        cap = buf.shape[0]
+        k = int(n.value)
+        if k <= cap:
+            return buf[:k].copy()
+        start = k % cap
+        return np.concatenate([buf[start:], buf[:start]])
 
     def profile_start(self, max_stages: int) -> None:
         check(load().osb_profile_start(self.handle, int(max_stages)), "osb_profile_start")

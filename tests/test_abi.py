@@ -102,6 +102,8 @@ def test_buffer_checks(osb):
     assert L.osb_diagnostics(None, None) == 1
     assert L.osb_batch_step(None, 1, 1) == 1
     assert L.osb_set_boundaries(None, 0, 0, 0) == 1
+    assert L.osb_set_diag_series(None, None, 0) == 1
+    assert L.osb_diag_series_count(None, None) == 1
 
 
 def test_binding_refuses_missing_library(osb, tmp_path):
