@@ -251,6 +251,8 @@ def time_steps(torch, g, steps, warmup, profile=False):
 
 
 def ke_series(torch, g, steps):
+    """E_k after each step from the FP64 accumulator (the separate reduction:
+    the FP32 path's fused series would add its own FP32 evaluation error)."""
     out = [g.diagnostics()["ke"]]
     for _ in range(steps):
         g.step(1)

@@ -38,7 +38,8 @@ def _grid(osb, torch, n, order, precision, dt, seed, amp, Re=1600.0, Mach=0.1):
 
 def tgv_curves(n: int, order: int, precision: str, t_end: float, every: int = 50, dt: float | None = None,
                seed: int = 1234, amp: float = 1e-4) -> dict:
-    """E_k, enstrophy and max CFL every `every` steps up to t_end."""
+    """E_k, enstrophy and max CFL every `every` steps up to t_end, and E_k and
+    enstrophy of every step (the series fused into the first RK stage)."""
     import torch
     from . import osb
     osb.load()
@@ -47,8 +48,10 @@ def tgv_curves(n: int, order: int, precision: str, t_end: float, every: int = 50
     g = _grid(osb, torch, n, order, prec, dt, seed, amp)
     nsteps = int(round(t_end / dt))
     t, ke, ens, cfl = [], [], [], []
+    step_series = []
     d = g.diagnostics()
     t.append(d["t"]), ke.append(d["ke"]), ens.append(d["enstrophy"]), cfl.append(d["max_cfl"])
+    g.set_diag_series(every)
     done = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -56,13 +59,19 @@ def tgv_curves(n: int, order: int, precision: str, t_end: float, every: int = 50
         k = min(every, nsteps - done)
         g.step(k)
         done += k
+        step_series.append(g.diag_series()[-k:])
         d = g.diagnostics()
         t.append(d["t"]), ke.append(d["ke"]), ens.append(d["enstrophy"]), cfl.append(d["max_cfl"])
     seconds = time.perf_counter() - t0
     del g
     torch.cuda.empty_cache()
+    # per step: the state at the start of steps 0 .. nsteps-1, plus the final state
+    ser = np.concatenate(step_series)
+    ke_step = ser[:, 0].tolist() + [ke[-1]]
+    ens_step = ser[:, 1].tolist() + [ens[-1]]
     return dict(n=n, order=order, precision=precision, dt=dt, steps=nsteps, every=every, t=t, ke=ke,
-                enstrophy=ens, max_cfl=cfl, seconds=seconds, point_stages_per_s=3.0 * n ** 3 * nsteps / seconds)
+                enstrophy=ens, max_cfl=cfl, seconds=seconds, point_stages_per_s=3.0 * n ** 3 * nsteps / seconds,
+                t_step=[i * dt for i in range(nsteps + 1)], ke_step=ke_step, enstrophy_step=ens_step)
 
 
 def dissipation(t, ke):
@@ -72,7 +81,10 @@ def dissipation(t, ke):
 
 
 def summarize(c: dict) -> dict:
-    t, ke, ens = np.asarray(c["t"]), np.asarray(c["ke"]), np.asarray(c["enstrophy"])
+    if "ke_step" in c:  # every step
+        t, ke, ens = np.asarray(c["t_step"]), np.asarray(c["ke_step"]), np.asarray(c["enstrophy_step"])
+    else:
+        t, ke, ens = np.asarray(c["t"]), np.asarray(c["ke"]), np.asarray(c["enstrophy"])
     eps = dissipation(t, ke)
     i_eps, i_ens = int(np.argmax(eps)), int(np.argmax(ens))
     at = {}
@@ -92,8 +104,9 @@ def summarize(c: dict) -> dict:
 def compare_curves(a: dict, ref: dict) -> dict:
     """KE-decay error of run a against the reference run: max_t |E_k - E_k^ref| / E_k^ref(0),
     and the same for the dissipation rate relative to its peak."""
-    ka, kr = np.asarray(a["ke"]), np.asarray(ref["ke"])
-    ea, er = dissipation(a["t"], ka), dissipation(ref["t"], kr)
+    key, tk = ("ke_step", "t_step") if "ke_step" in a and "ke_step" in ref else ("ke", "t")
+    ka, kr = np.asarray(a[key]), np.asarray(ref[key])
+    ea, er = dissipation(a[tk], ka), dissipation(ref[tk], kr)
     return dict(ke_err=float(np.max(np.abs(ka - kr)) / kr[0]),
                 eps_err=float(np.max(np.abs(ea - er)) / np.max(np.abs(er))),
                 speedup=ref["seconds"] / a["seconds"])
