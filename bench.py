@@ -166,7 +166,7 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # Oracle timing (the CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def time_oracle(w, target_s=12.0, max_n=None):
+def time_oracle(w, target_s=12.0, max_n=None, single_core=False):
     """Times the CPU oracle on a bounded sample of the workload: one RK3 step on
     the largest cubic grid (<= the workload's) whose step fits ~target_s."""
     from oracle import oracle as orc
@@ -185,9 +185,25 @@ def time_oracle(w, target_s=12.0, max_n=None):
     t0 = time.perf_counter()
     orc.rk3_step(case, Q, 1)
     dt = time.perf_counter() - t0
-    return dict(value=3 * n ** 3 / dt, unit=UNIT, cores=orc.get_threads(), kind="oracle",
-                sample=f"1 RK3 step (3 stages) of the same Taylor-Green case on a {n}^3 grid, "
-                       f"order {w['order']}, FP64, {dt:.2f} s on {orc.get_threads()} OpenMP threads")
+    out = dict(value=3 * n ** 3 / dt, unit=UNIT, cores=orc.get_threads(), kind="oracle",
+               sample=f"1 RK3 step (3 stages) of the same Taylor-Green case on a {n}^3 grid, "
+                      f"order {w['order']}, FP64, {dt:.2f} s on {orc.get_threads()} OpenMP threads")
+    if single_core:
+        # the same on one core, on a smaller sample (about a second)
+        threads = orc.get_threads()
+        orc.set_threads(1)
+        try:
+            n1 = max(16, min(n, int((1.0 / (per_pt * threads)) ** (1 / 3))))
+            case1 = orc.Case(n1, n1, n1, order=w["order"], Re=w["Re"], Mach=w["Mach"], dt=w["dt"])
+            Q1 = orc.tgv_init(case1, inputs.gaussian_noise(n1, n1, n1, w["noise_seed"]), w["noise_amp"])
+            t0 = time.perf_counter()
+            orc.rk3_step(case1, Q1, 1)
+            dt1 = time.perf_counter() - t0
+        finally:
+            orc.set_threads(threads)
+        out["single_core"] = dict(value=3 * n1 ** 3 / dt1, unit=UNIT, cores=1,
+                                  sample=f"1 RK3 step on a {n1}^3 grid, {dt1:.2f} s on 1 thread")
+    return out
 
 
 def run_reference(args):
@@ -265,11 +281,7 @@ def ensemble_specs(count=64, seed=7):
     [100, 3200], M in [0.05, 0.3]; dt = 3.385e-3 (64/N) 11/(1 + 1/M) keeps the
     paper's acoustic Courant number of the 64^3, M = 0.1 case."""
     from paper_1609_01277_gb300 import inputs
-    out = []
-    for e in inputs.ensemble(count, seed):
-        e["dt"] = BASE_DT_64 * (64.0 / e["n"]) * 11.0 / (1.0 + 1.0 / e["Mach"])
-        out.append(e)
-    return out
+    return inputs.ensemble_with_dt(count, seed, BASE_DT_64)
 
 
 def run_ensemble(torch, osb, inputs, steps, precision):
@@ -504,6 +516,16 @@ def run_ours(args):
         del gE
         variants["euler_order4_fp64"] = {"value": args.steps * npts / (msE * 1e-3), "ms_per_step": msE / args.steps,
                                          "stages_per_step": 1}
+        # the 32^3 parity case (20 steps of dt 3.385e-3, no noise): it fits in
+        # L2, so it is a latency figure, not a roofline one
+        g32 = osb.Grid(osb.Config(32, 32, 32, order=4, precision=osb.OSB_FP64, Re=w["Re"], Mach=w["Mach"],
+                                  gamma=w["gamma"], Pr=w["Pr"], dt=3.385e-3))
+        g32.init_taylor_green()
+        ms32, _ = time_steps(torch, g32, 20, args.warmup)
+        del g32
+        variants["tgv_32^3_order4_fp64_20steps"] = {
+            "value": 20 * 3 * 32 ** 3 / (ms32 * 1e-3), "ms_per_step": ms32 / 20,
+            "note": "3 stages x 3 kernels per step, replayed as one CUDA graph per step"}
         # kinetic energy and enstrophy of every step, fused into the first stage
         for prec in ("fp64", "fp32"):
             gD = make_grid(osb, w, 4, prec, noise_dev)
@@ -551,7 +573,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = time_oracle(w)
+        cpu = time_oracle(w, single_core=True)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -198,6 +198,61 @@ def step_timing(n: int, order: int, precision: str, steps: int, warmup: int = 3)
                 kernel_ms={k: v["total_ms"] / max(v["launches"], 1) for k, v in prof.items()})
 
 
+def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count: int = 64, seed: int = 7) -> dict:
+    """The uneven Taylor-Green ensemble (64 grids of 32^3..128^3, Re in
+    [100, 3200], M in [0.05, 0.3], order 4) advanced `steps` RK3 steps by
+    osb_batch_step in chunks of `every` (one persistent launch per chunk),
+    with every grid's E_k after each chunk.  Per precision: time, point-stages
+    per second; FP32 against FP64: the KE-decay error max over grids and
+    chunks of |E_k - E_k^FP64| / E_k^FP64(0), and the speed-up."""
+    import torch
+    from . import inputs, osb
+    osb.load()
+    specs = inputs.ensemble_with_dt(count, seed)
+    out = {}
+    for precision in precisions:
+        prec = {"fp64": osb.OSB_FP64, "fp32": osb.OSB_FP32, "df64": osb.OSB_DF64}[precision]
+        grids = []
+        for i, e in enumerate(specs):
+            n = e["n"]
+            g = osb.Grid(osb.Config(n, n, n, order=4, precision=prec, Re=e["Re"], Mach=e["Mach"], dt=e["dt"]))
+            g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
+            grids.append(g)
+        tuned = {}
+        for g in grids:
+            if g.cfg.nx not in tuned:
+                tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
+        for i, g in enumerate(grids):  # autotuning stepped the grids: start again
+            n = g.cfg.nx
+            g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
+        ke = [[g.diagnostics()["ke"] for g in grids]]
+        seconds, done = 0.0, 0
+        while done < steps:
+            k = min(every, steps - done)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            osb.batch_step(grids, k)
+            seconds += time.perf_counter() - t0
+            done += k
+            ke.append([g.diagnostics()["ke"] for g in grids])
+        pts = sum(g.cfg.n for g in grids)
+        out[precision] = dict(steps=steps, points=pts, seconds=seconds, tile_depth=tuned,
+                              point_stages_per_s=3.0 * pts * steps / seconds, ke=ke)
+        del grids
+        torch.cuda.empty_cache()
+    if "fp64" in out:
+        ref = np.asarray(out["fp64"]["ke"])
+        for p in out:
+            if p == "fp64":
+                continue
+            k = np.asarray(out[p]["ke"])
+            out[p]["ke_err_vs_fp64"] = float(np.max(np.abs(k - ref) / ref[0][None, :]))
+            out[p]["speedup_vs_fp64"] = out["fp64"]["seconds"] / out[p]["seconds"]
+    for p in out:
+        out[p].pop("ke")
+    return out
+
+
 def closure_timing(n: int, reps: int, warmup: int = 2) -> dict:
     """Learned-closure network on an n^3 grid: CUDA-event time of one forward
     pass and of one loss + gradient evaluation (BF16 tensor-core convolutions),
@@ -256,6 +311,10 @@ def main(argv=None):
     cl = sub.add_parser("closure")
     cl.add_argument("--n", type=int, default=64)
     cl.add_argument("--reps", type=int, default=10)
+    en = sub.add_parser("ensemble")
+    en.add_argument("--steps", type=int, default=500)
+    en.add_argument("--every", type=int, default=50)
+    en.add_argument("--precisions", default="fp64,fp32")
     e = sub.add_parser("fp32-error")
     e.add_argument("--n", type=int, default=512)
     e.add_argument("--order", type=int, default=8)
@@ -272,6 +331,8 @@ def main(argv=None):
         print(json.dumps(res))
     elif args.cmd == "steps":
         print(json.dumps(step_timing(args.n, args.order, args.precision, args.steps, args.warmup)))
+    elif args.cmd == "ensemble":
+        print(json.dumps(ensemble_run(args.steps, tuple(args.precisions.split(",")), args.every)))
     elif args.cmd == "closure":
         print(json.dumps(closure_timing(args.n, args.reps)))
     elif args.cmd == "scalar":

@@ -59,3 +59,14 @@ def ensemble(count: int, seed: int, sizes=(32, 48, 64, 96, 128),
     re = rng.uniform(*re_range, size=count)
     mach = rng.uniform(*mach_range, size=count)
     return [dict(n=int(n[i]), Re=float(re[i]), Mach=float(mach[i])) for i in range(count)]
+
+
+def ensemble_with_dt(count: int = 64, seed: int = 7, base_dt_64: float = 3.385e-3):
+    """The uneven ensemble with a time step per instance: the 64^3, M = 0.1
+    step scaled by 64/N and by 11/(1 + 1/M), which keeps the acoustic Courant
+    number of that case (sound speed ~ 1/M, flow speed ~ 1)."""
+    out = []
+    for e in ensemble(count, seed):
+        e["dt"] = base_dt_64 * (64.0 / e["n"]) * 11.0 / (1.0 + 1.0 / e["Mach"])
+        out.append(e)
+    return out
