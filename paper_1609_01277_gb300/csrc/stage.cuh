@@ -639,6 +639,19 @@ __device__ __forceinline__ void acc_d2(dd_acc &acc, const P *__restrict__ f, con
 // parity bits of the conserved fields rho, rho u, rho v, rho w, rho E
 __device__ __forceinline__ constexpr int q_parity(int m) { return m == 1 ? PAR_X : (m == 2 ? PAR_Y : (m == 3 ? PAR_Z : PAR_EVEN)); }
 
+// One axis of the advective half (double-float): acc_m += h D_AX q_m, and the
+// mass flux -(1/2) D_AX (rho u_AX).
+template <int R, int AX, int POL, typename S, bool SYM>
+__device__ __forceinline__ void adv_axis_dd(dd_acc (&acc)[5], const S *Q, size_t qs, const Nbr<R, SYM> &nb,
+                                            const Coef<dd> &c, const dd &h) {
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const dd d = D1<R, AX, POL>(Q + m * qs, nb, c, q_parity(m));
+        acc[m].add_prod(h, d.hi, d.lo);
+        if (m == 1 + AX) acc[0].add_prod(dd(-0.5f, 0.f), d.hi, d.lo);
+    }
+}
+
 template <int POL, typename S, int R, bool VB, bool SYM>
 __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R, SYM> &nb, int i, dd (&res)[5]) {
     const Coef<dd> &c = a.cdd;
@@ -651,21 +664,16 @@ __device__ __forceinline__ void resid_terms_dd(const StageArgs &a, const Nbr<R, 
     const dd hu = dd_scale(u, -0.5f), hv = dd_scale(v, -0.5f), hw = dd_scale(w, -0.5f), hdiv = dd_scale(div, -0.5f);
     dd_acc acc[5];
     // advective + dilatation half of the skew-symmetric form; mass flux
+    // (axis by axis: one derivative live at a time)
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        const S *f = Q + m * qs;
-        const int pm = q_parity(m);
-        const dd dx = D1<R, 0, POL>(f, nb, c, pm), dy = D1<R, 1, POL>(f, nb, c, pm), dz = D1<R, 2, POL>(f, nb, c, pm);
-        acc[m].add_prod(hu, dx.hi, dx.lo);
-        acc[m].add_prod(hv, dy.hi, dy.lo);
-        acc[m].add_prod(hw, dz.hi, dz.lo);
-        dd qc = ld<POL, dd>(f + i);
+        dd qc = ld<POL, dd>(Q + m * qs + i);
         if (m == 4) qc = qc + a.kdd.e_ref;  // the full rho E multiplies div u
         acc[m].add_prod(hdiv, qc.hi, qc.lo);
-        if (m == 1) acc[0].add_prod(dd(-0.5f, 0.f), dx.hi, dx.lo);
-        if (m == 2) acc[0].add_prod(dd(-0.5f, 0.f), dy.hi, dy.lo);
-        if (m == 3) acc[0].add_prod(dd(-0.5f, 0.f), dz.hi, dz.lo);
     }
+    adv_axis_dd<R, 0, POL>(acc, Q, qs, nb, c, hu);
+    adv_axis_dd<R, 1, POL>(acc, Q, qs, nb, c, hv);
+    adv_axis_dd<R, 2, POL>(acc, Q, qs, nb, c, hw);
     // momentum fluxes -D_j Phi_ij and energy flux -D_j F'_j - c_ref div u
     const dd *Pxx = aux + A_PXX * as, *Pyy = aux + A_PYY * as, *Pzz = aux + A_PZZ * as;
     const dd *Pxy = aux + A_PXY * as, *Pxz = aux + A_PXZ * as, *Pyz = aux + A_PYZ * as;
