@@ -898,12 +898,13 @@ __global__ void __launch_bounds__(BX *BY) k_resid(const StageArgs a) {
     resid_point<LD_NC, S, T, R, MODE, VB, SYM>(a, x, y, z);
 }
 
-// Double-float residual kernel with explicit occupancy targets: three CTAs per
-// SM up to order 4 (a few spilled registers buy 24 resident warps to hide the
-// neighbour-load latency this kernel waits on), two for orders 6 and 8, one
-// (all registers, no spills) for orders 10 and 12.
+// Double-float residual kernel with explicit occupancy targets: four CTAs per
+// SM up to order 4 (64 registers, a few bytes spilled, 32 resident warps to
+// hide the neighbour-load latency this kernel waits on), two for orders 6 and
+// 8 (three spill hundreds of bytes and measured slower at order 8), one (all
+// registers, no spills) for orders 10 and 12.
 template <typename S, int R, int MODE, bool VB, bool SYM>
-__global__ void __launch_bounds__(BX *BY, R <= 2 ? 3 : (R <= 4 ? 2 : 1)) k_resid_dd(const StageArgs a) {
+__global__ void __launch_bounds__(BX *BY, R <= 2 ? 4 : (R <= 4 ? 2 : 1)) k_resid_dd(const StageArgs a) {
     const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y, z = blockIdx.z;
     if (x >= a.d.nx || y >= a.d.ny) return;
     resid_point<LD_NC, S, dd, R, MODE, VB, SYM>(a, x, y, z);
