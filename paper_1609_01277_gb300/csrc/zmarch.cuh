@@ -2,7 +2,7 @@
 // work form A), the memory-lean form of the three kernels in stage.cuh.
 //
 // Each CTA owns a TX x TY column tile of the grid and a chunk of z planes.
-// Planes stream through a shared-memory ring PF planes ahead of their use,
+// Planes stream through a shared-memory ring one or two planes ahead of their use,
 // over the tile plus a halo (R rows in y; 4 columns in x, so that every row
 // starts on a 16-byte boundary).  Tiles away from the periodic boundary load
 // each field's plane with one TMA box copy (cp.async.bulk.tensor.3d) that
@@ -31,7 +31,6 @@ namespace osb {
 namespace zm {
 
 constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int PF = 1;   // planes in flight ahead of the lead plane
 constexpr int CX = 4;   // ring column of the tile's first x (row start x0 - 4 is 16-byte aligned)
 constexpr unsigned ZM_WAIT_LIMIT = 1u << 24;
 
@@ -39,6 +38,10 @@ template <int R>
 struct Geo {
     static constexpr int RW = TX + 2 * CX, RH = TY + 2 * R, RA = RW * RH;
     static constexpr int RAP = (RA + 31) / 32 * 32;  // ring plane stride: TMA destinations need 128-byte alignment
+    // planes in flight ahead of the lead plane: two, except at radius 2, where
+    // the second ring slot would leave room for one CTA per SM instead of two
+    // (measured at 256^3: radius 1, 3, 4 gain 3-4% with two; radius 2 loses 40%)
+    static constexpr int PF = (R == 2) ? 1 : 2;
     static constexpr int NS = R + 1 + PF;            // ring slots
 };
 
@@ -264,7 +267,7 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
             if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
             phase ^= 1u << s;
         } else {
-            cp_wait<PF - 1>();
+            cp_wait<G::PF - 1>();
         }
     };
 
@@ -274,7 +277,7 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
 
     const int Lbeg = z0 - R, Lend = z1 + R;  // lead planes [Lbeg, Lend)
 #pragma unroll 1
-    for (int p = 0; p < PF; ++p) issue(Lbeg + p);
+    for (int p = 0; p < G::PF; ++p) issue(Lbeg + p);
     const FoldW<float> &fw = a.f32;
     // first-stage diagnostics: this thread's sums of (1/2) rho u.u and
     // (1/2) rho |omega|^2 over its column, in FP64
@@ -284,8 +287,8 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
     for (int L = Lbeg; L < Lend; ++L) {
         wait_plane(L);
         __syncthreads();
-        if (L + PF < Lend)
-            issue(L + PF);
+        if (L + G::PF < Lend)
+            issue(L + G::PF);
         else if (!use_tma)
             cp_commit();  // keep the group count uniform
         const int sL = ((L % G::NS) + G::NS) % G::NS;
@@ -446,7 +449,7 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
             if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
             phase ^= 1u << s;
         } else {
-            cp_wait<PF - 1>();
+            cp_wait<G::PF - 1>();
         }
     };
 
@@ -466,13 +469,13 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
 
     const int Lbeg = z0 - R, Lend = z1 + R;
 #pragma unroll 1
-    for (int p = 0; p < PF; ++p) issue(Lbeg + p);
+    for (int p = 0; p < G::PF; ++p) issue(Lbeg + p);
 #pragma unroll 1
     for (int L = Lbeg; L < Lend; ++L) {
         wait_plane(L);
         __syncthreads();
-        if (L + PF < Lend)
-            issue(L + PF);
+        if (L + G::PF < Lend)
+            issue(L + G::PF);
         else if (!use_tma)
             cp_commit();
         const int sL = ((L % G::NS) + G::NS) % G::NS;
