@@ -42,10 +42,11 @@ template <typename T, int R, bool VB>
 __global__ void __launch_bounds__(BX *BY) k_batch(const BatchParams P) {
     batch_loop<T, R, VB>(P);
 }
-// double-float items: three CTAs per SM at orders 2-4, form A (80 registers,
-// about 100 bytes spilled; measured faster than two), else two (128 registers)
+// double-float items: bounded to two CTAs per SM (128 registers, no spills;
+// three, with about 100 bytes spilled at order 4, measured the same within
+// run-to-run spread)
 template <int R, bool VB>
-__global__ void __launch_bounds__(BX *BY, (R <= 2 && !VB) ? 3 : 2) k_batch_dd(const BatchParams P) {
+__global__ void __launch_bounds__(BX *BY, 2) k_batch_dd(const BatchParams P) {
     batch_loop<dd, R, VB>(P);
 }
 
