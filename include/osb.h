@@ -12,7 +12,9 @@
  *    fields (rho, rho*u0, rho*u1, rho*u2, rho*E), FP64, no padding; N = nx*ny*nz
  *    points per field, so a host state is 5*N doubles.
  *  - Grid: domain [0, 2*pi)^3, x_i = i*h_a with h_a = 2*pi/n_a per axis, periodic
- *    in every direction (Section 2.2 grid, Section 2.6 periodic boundaries).
+ *    in every direction (Section 2.2 grid, Section 2.6 periodic boundaries),
+ *    unless osb_set_boundaries puts symmetry planes on an axis (that axis is
+ *    then [0, pi] with x_i = (i + 1/2) pi/n_a).
  *  - Device memory is owned by the caller (for example allocated by PyTorch):
  *    the library never allocates or frees device memory.  The caller passes
  *    one state buffer and one workspace buffer per grid, sized by
