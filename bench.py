@@ -59,7 +59,10 @@ def workload(args):
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic work per point-stage (counted from the kernel source; FMA = 2)
+# Algorithmic work per point-stage: the operations of the stage as the
+# equations define it (FMA = 2).  The kernels fold some constant factors into
+# precomputed stencil weights and so issue fewer; the roofline divides this
+# fixed count by their time.
 # ---------------------------------------------------------------------------
 def resid_flops_per_point(r: int) -> int:
     d1 = 3 * r          # r subtractions + r FMAs
