@@ -75,14 +75,6 @@ template <typename T>
 __device__ __forceinline__ T k_gM2(const StageArgs &a) {
     if constexpr (is_dd<T>) return a.kdd.gM2; else return T(a.ph.gM2);
 }
-template <typename T>
-__device__ __forceinline__ T k_inv_re(const StageArgs &a) {
-    if constexpr (is_dd<T>) return a.kdd.inv_re; else return T(a.ph.inv_re);
-}
-template <typename T>
-__device__ __forceinline__ T k_kappa(const StageArgs &a) {
-    if constexpr (is_dd<T>) return a.kdd.kappa; else return T(a.ph.kappa);
-}
 
 __device__ __forceinline__ int wrapc(int i, int n) {
     i %= n;

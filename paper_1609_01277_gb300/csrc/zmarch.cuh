@@ -111,7 +111,7 @@ __device__ __forceinline__ void qpush(float (&q)[N], float v) {
     q[N - 1] = v;
 }
 
-// z derivatives from a register queue centred at index R.
+// z first derivative from a register queue centred at index R.
 template <int R>
 __device__ __forceinline__ float qd1(const float (&q)[2 * R + 1], const float *c) {
     float s = 0.f;
@@ -119,14 +119,7 @@ __device__ __forceinline__ float qd1(const float (&q)[2 * R + 1], const float *c
     for (int k = R; k >= 1; --k) s = fmaf(c[k], q[R + k] - q[R - k], s);
     return s;
 }
-template <int R>
-__device__ __forceinline__ float qd2(const float (&q)[2 * R + 1], const float *c) {
-    float s = c[0] * q[R];
-#pragma unroll
-    for (int k = R; k >= 1; --k) s = fmaf(c[k], q[R + k] + q[R - k], s);
-    return s;
-}
-// x / y derivatives from a shared-memory plane (rectangle layout).
+// x / y first derivatives from a shared-memory plane (rectangle layout).
 template <int R>
 __device__ __forceinline__ float sdx1(const float *p, int ce, const float *c) {
     float s = 0.f;
@@ -140,21 +133,6 @@ __device__ __forceinline__ float sdy1(const float *p, int ce, const float *c) {
     float s = 0.f;
 #pragma unroll
     for (int k = R; k >= 1; --k) s = fmaf(c[k], p[ce + k * W] - p[ce - k * W], s);
-    return s;
-}
-template <int R>
-__device__ __forceinline__ float sdx2(const float *p, int ce, const float *c) {
-    float s = c[0] * p[ce];
-#pragma unroll
-    for (int k = R; k >= 1; --k) s = fmaf(c[k], p[ce + k] + p[ce - k], s);
-    return s;
-}
-template <int R>
-__device__ __forceinline__ float sdy2(const float *p, int ce, const float *c) {
-    constexpr int W = Geo<R>::RW;
-    float s = c[0] * p[ce];
-#pragma unroll
-    for (int k = R; k >= 1; --k) s = fmaf(c[k], p[ce + k * W] + p[ce - k * W], s);
     return s;
 }
 
