@@ -198,7 +198,8 @@ def step_timing(n: int, order: int, precision: str, steps: int, warmup: int = 3)
                 kernel_ms={k: v["total_ms"] / max(v["launches"], 1) for k, v in prof.items()})
 
 
-def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count: int = 64, seed: int = 7) -> dict:
+def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count: int = 64, seed: int = 7,
+                 autotune: bool = True) -> dict:
     """The uneven Taylor-Green ensemble (64 grids of 32^3..128^3, Re in
     [100, 3200], M in [0.05, 0.3], order 4) advanced `steps` RK3 steps by
     osb_batch_step in chunks of `every` (one persistent launch per chunk),
@@ -219,7 +220,7 @@ def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count
             g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
             grids.append(g)
         tuned = {}
-        for g in grids:
+        for g in grids if autotune else []:
             if g.cfg.nx not in tuned:
                 tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
         for i, g in enumerate(grids):  # autotuning stepped the grids: start again
@@ -315,6 +316,8 @@ def main(argv=None):
     en.add_argument("--steps", type=int, default=500)
     en.add_argument("--every", type=int, default=50)
     en.add_argument("--precisions", default="fp64,fp32")
+    en.add_argument("--count", type=int, default=64)
+    en.add_argument("--no-autotune", action="store_true")
     e = sub.add_parser("fp32-error")
     e.add_argument("--n", type=int, default=512)
     e.add_argument("--order", type=int, default=8)
@@ -332,7 +335,8 @@ def main(argv=None):
     elif args.cmd == "steps":
         print(json.dumps(step_timing(args.n, args.order, args.precision, args.steps, args.warmup)))
     elif args.cmd == "ensemble":
-        print(json.dumps(ensemble_run(args.steps, tuple(args.precisions.split(",")), args.every)))
+        print(json.dumps(ensemble_run(args.steps, tuple(args.precisions.split(",")), args.every, args.count,
+                                      autotune=not args.no_autotune)))
     elif args.cmd == "closure":
         print(json.dumps(closure_timing(args.n, args.reps)))
     elif args.cmd == "scalar":
