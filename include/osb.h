@@ -238,7 +238,10 @@ osb_status osb_batch_configure(double wait_limit_seconds, int test_stall);
 osb_status osb_autotune(osb_grid *grid, int trial_steps, int *best_tz);
 
 /* Diagnostics of a caller-provided state without any device allocation and
- * without a grid object.  The paper has no counterpart: this entry point exists
+ * without a grid object.  The state is read as a fully periodic box
+ * [0, 2 pi)^3 (h = 2 pi / n, wrapped stencils); states of grids with symmetry
+ * planes (osb_set_boundaries) must use osb_diagnostics instead, since this
+ * call has no boundary argument and would return wrong enstrophy and CFL.  The paper has no counterpart: this entry point exists
  * for callers that cannot allocate device memory at the point where they need
  * the diagnostics -- for example code running while a stream is captured into
  * a CUDA graph in global capture mode (where cudaMalloc is an error that
@@ -256,15 +259,28 @@ osb_status osb_autotune(osb_grid *grid, int trial_steps, int *best_tz);
  * Scratch: a fixed device array of 1216 partial-sum records (155,648 bytes)
  * inside the library, held on every device that loads the library until the
  * process exits.  Every admissible grid (nx*ny*nz < 2^31, each >= 1) fits it;
- * larger or invalid sizes are rejected with OSB_ERR_INVALID_ARG before any GPU
- * work.  The first call on a device looks up the array's device address (no
- * allocation); make that first call before any stream capture begins.  All
+ * larger or invalid sizes are rejected with OSB_ERR_INVALID_ARG, pointers not
+ * 8-byte aligned with OSB_ERR_BUFFER, both before any GPU work.  Every call
+ * looks up the array's device address on the current device (no allocation);
+ * the first call on a device may load the library's device code, so make it
+ * before any stream capture begins.  All
  * calls share the one array, so calls whose kernels overlap on the GPU (for
  * example on two streams at once) race and give wrong results; serialise them.
  * No allocation of any kind: no cudaMalloc, cudaFree or allocating library
  * routine is called. */
 osb_status osb_diagnostics_noalloc(const double *Q_dev, int nx, int ny, int nz, int order,
                                    const osb_params *params, double *out_dev, void *cuda_stream);
+
+/* Measurement utility (no counterpart in the paper): the FP64 fused
+ * multiply-add rate of the device, the roofline denominator of the FP64 stage
+ * kernels.  One launch of `blocks` blocks of 256 threads; each thread runs 8
+ * independent FMA chains for 16*iters steps and writes one double to out_dev.
+ * flops = blocks * 256 * 8 * 16 * iters * 2; the caller times the launch on
+ * cuda_stream (the call does not synchronise).
+ *  out_dev: device, blocks*256 FP64 values, caller-owned, overwritten.
+ * Errors: NULL or unaligned out_dev, blocks < 1 or iters < 1 ->
+ * OSB_ERR_INVALID_ARG; a failed launch -> OSB_ERR_CUDA. */
+osb_status osb_fp64_rate_probe(double *out_dev, int blocks, int iters, void *cuda_stream);
 
 /* ------------------------------------------------------------------------
  * Scalar advection-diffusion on the periodic box [0, 2 pi)^3: the equation of

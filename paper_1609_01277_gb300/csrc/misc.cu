@@ -1,8 +1,6 @@
 // misc.cu -- Taylor-Green initial state and FP64 diagnostics reductions.
 #include <math.h>
 
-#include <mutex>
-
 #include "stage.cuh"
 
 namespace osb {
@@ -22,8 +20,10 @@ __device__ __forceinline__ double axis_coord(int i, int n, bool sym) {
 
 __global__ void k_init_tgv(const Dims d, const Phys ph, double *__restrict__ U, size_t s,
                            const double *__restrict__ noise, double amp) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
-        const int x = i % d.nx, y = (i / d.nx) % d.ny, z = i / (d.nx * d.ny);
+    // 64-bit index: i + stride must not overflow for grids near 2^31 points
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % d.nx), y = (int)((i / d.nx) % d.ny), z = (int)(i / ((long long)d.nx * d.ny));
         const double X = axis_coord(x, d.nx, d.sym & 1), Y = axis_coord(y, d.ny, d.sym & 2);
         const double Z = axis_coord(z, d.nz, d.sym & 4);
         double sx, cx, sy, cy, sz, cz;
@@ -57,14 +57,14 @@ cudaError_t launch_init_tgv(const Dims &d, const Phys &ph, double *U, size_t str
 // FP32 copy of the FP64 accumulator (round to nearest), the stage-1 stencil
 // source of the FP32 path.
 __global__ void k_to_f32(const double *__restrict__ U, size_t us, float *__restrict__ q, size_t qs, int n) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
 #pragma unroll
         for (int m = 0; m < 5; ++m) q[m * qs + i] = d2f_bits(U[m * us + i]);
 }
 
 // Double-float copy of the accumulator; the energy field as rho E - e_ref.
 __global__ void k_to_dd(const double *__restrict__ U, size_t us, dd *__restrict__ q, size_t qs, int n, double e_ref) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) q[m * qs + i] = dd(U[m * us + i]);
         q[4 * qs + i] = dd(U[4 * us + i] - e_ref);
@@ -192,8 +192,9 @@ __global__ void __launch_bounds__(DIAG_THREADS)
     const double ih[3] = {d.nx / ((d.sym & 1) ? pi : two_pi), d.ny / ((d.sym & 2) ? pi : two_pi),
                           d.nz / ((d.sym & 4) ? pi : two_pi)};
     const double *rho = U, *m0 = U + s, *m1 = U + 2 * s, *m2 = U + 3 * s, *e = U + 4 * s;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < d.n; i += gridDim.x * blockDim.x) {
-        const int x = i % d.nx, y = (i / d.nx) % d.ny, z = i / (d.nx * d.ny);
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(i % d.nx), y = (int)((i / d.nx) % d.ny), z = (int)(i / ((long long)d.nx * d.ny));
         const double r = rho[i];
         const double u0 = m0[i] / r, u1 = m1[i] / r, u2 = m2[i] / r;
         const double uu = u0 * u0 + u1 * u1 + u2 * u2;
@@ -285,26 +286,16 @@ cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const C
 constexpr int NOALLOC_RECORDS = DIAG_MAX_BLOCKS;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_RECORDS * DIAG_STRIDE];
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static std::mutex g_noalloc_mu;
-static double *g_noalloc_ptr[NOALLOC_MAX_DEVICES];
-
 // Device address of the scratch array on the current device.  In host code
 // the name g_noalloc_scratch is only a host-side stand-in, so the address is
-// looked up once per device (with that device current) and cached.
+// looked up with the device current.  The lookup allocates nothing and is
+// repeated on every call rather than cached, so a context that was torn down
+// and re-created (cudaDeviceReset) is served at the array's new address.
 static cudaError_t noalloc_scratch(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 
@@ -351,6 +342,45 @@ extern "C" osb_status osb_diagnostics_noalloc(const double *Q_dev, int nx, int n
                            NOALLOC_RECORDS, out_dev, (cudaStream_t)cuda_stream);
     if (e != cudaSuccess) {
         set_last_error("osb_diagnostics_noalloc: kernel launch failed");
+        return OSB_ERR_CUDA;
+    }
+    return OSB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 arithmetic-rate probe: every thread runs eight independent chains of
+// fused multiply-adds (x = x * a + b), enough independent work per warp to
+// keep the FP64 pipe busy, and writes its sum so that nothing is eliminated.
+// flops per launch = blocks * 256 threads * 8 chains * iters * 2.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fp64_rate(double *__restrict__ out, int iters, double a, double b) {
+    double x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+#pragma unroll 1
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+extern "C" osb_status osb_fp64_rate_probe(double *out_dev, int blocks, int iters, void *cuda_stream) {
+    using namespace osb;
+    if (!out_dev || blocks < 1 || iters < 1 || ((uintptr_t)out_dev & 7)) {
+        set_last_error("osb_fp64_rate_probe: need an 8-byte aligned output, blocks >= 1, iters >= 1");
+        return OSB_ERR_INVALID_ARG;
+    }
+    // a, b keep x bounded (x -> b / (1 - a)), so no value overflows
+    k_fp64_rate<<<blocks, 256, 0, (cudaStream_t)cuda_stream>>>(out_dev, iters, 0.999999, 1e-6);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_last_error("osb_fp64_rate_probe: launch failed");
         return OSB_ERR_CUDA;
     }
     return OSB_OK;

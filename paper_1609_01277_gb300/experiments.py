@@ -15,6 +15,7 @@ reads their FP64 diagnostics.  CLI:
 from __future__ import annotations
 
 import argparse
+import os
 import json
 import time
 
@@ -288,6 +289,47 @@ def closure_timing(n: int, reps: int, warmup: int = 2) -> dict:
                 forward_tflops=flops / (fwd_ms * 1e-3) / 1e12)
 
 
+def fp64_peak(blocks: int, iters: int, repeats: int) -> dict:
+    """The FP64 FMA rate measured by the library's probe kernel, with the SM
+    clock sampled by nvidia-smi while it runs, next to the rate the unit
+    counts give at the sampled clock (2 FP64 FMAs per SM per cycle)."""
+    import subprocess
+    import tempfile
+
+    import torch
+    from . import build, osb
+    build.build()
+    osb.load()
+    torch.cuda.set_device(0)
+    fd, path = tempfile.mkstemp(suffix=".csv")
+    os.close(fd)
+    proc = subprocess.Popen(["nvidia-smi", "--id=0", "--query-gpu=clocks.sm,clocks.max.sm",
+                             "--format=csv,noheader,nounits", "-lms", "50"], stdout=open(path, "w"),
+                            stderr=subprocess.DEVNULL)
+    try:
+        osb.fp64_rate(blocks, max(1, iters // 10), 1)  # warm-up, clocks ramp
+        r = osb.fp64_rate(blocks, iters, repeats)
+    finally:
+        proc.terminate()
+        proc.wait(timeout=5)
+    sm = []
+    with open(path) as f:
+        for line in f:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 2 and parts[0].replace(".", "").isdigit():
+                sm.append((float(parts[0]), float(parts[1])))
+    os.unlink(path)
+    busy = [a for a, _ in sm]
+    med = sorted(busy)[len(busy) // 2] if busy else None
+    props = torch.cuda.get_device_properties(0)
+    r["sm_mhz_median"] = med
+    r["sm_max_mhz"] = max((b for _, b in sm), default=None)
+    r["sms"] = props.multi_processor_count
+    if med:
+        r["unit_count_tflops_at_sampled_clock"] = 2 * 2 * props.multi_processor_count * med * 1e6 / 1e12
+    return r
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -318,6 +360,10 @@ def main(argv=None):
     en.add_argument("--precisions", default="fp64,fp32")
     en.add_argument("--count", type=int, default=64)
     en.add_argument("--no-autotune", action="store_true")
+    pk = sub.add_parser("fp64-peak")
+    pk.add_argument("--blocks", type=int, default=152 * 8)
+    pk.add_argument("--iters", type=int, default=2000)
+    pk.add_argument("--repeats", type=int, default=5)
     e = sub.add_parser("fp32-error")
     e.add_argument("--n", type=int, default=512)
     e.add_argument("--order", type=int, default=8)
@@ -339,6 +385,8 @@ def main(argv=None):
                                       autotune=not args.no_autotune)))
     elif args.cmd == "closure":
         print(json.dumps(closure_timing(args.n, args.reps)))
+    elif args.cmd == "fp64-peak":
+        print(json.dumps(fp64_peak(args.blocks, args.iters, args.repeats)))
     elif args.cmd == "scalar":
         print(json.dumps(scalar_timing(args.n, args.order, args.steps, args.warmup)))
     else:

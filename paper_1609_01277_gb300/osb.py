@@ -34,7 +34,7 @@ EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_gri
            "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_set_dissipative", "osb_closure_set_loss_weight", "osb_closure_status", "osb_closure_sync_weights",
            "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
            "osb_box_filter", "osb_scalar_rk3", "osb_set_boundaries", "osb_set_diag_series",
-           "osb_diag_series_count", "osb_profile_start", "osb_profile_stop",
+           "osb_diag_series_count", "osb_profile_start", "osb_profile_stop", "osb_fp64_rate_probe",
            "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
@@ -101,6 +101,7 @@ def load(path: str | None = None):
     L.osb_diag_series_count.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
     L.osb_profile_start.argtypes = [vp, ctypes.c_int]
     L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
+    L.osb_fp64_rate_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
     L.osb_status_string.argtypes = [ctypes.c_int]
     L.osb_status_string.restype = ctypes.c_char_p
     L.osb_last_error.restype = ctypes.c_char_p
@@ -331,3 +332,26 @@ def autotune(grid: "Grid", trial_steps: int = 3) -> int:
     tz = ctypes.c_int(0)
     check(load().osb_autotune(grid.handle, int(trial_steps), ctypes.byref(tz)), "osb_autotune")
     return tz.value
+
+
+def fp64_rate(blocks: int = 152 * 8, iters: int = 2000, repeats: int = 5) -> dict:
+    """Measured FP64 fused multiply-add rate (TFLOP/s): the library's probe
+    kernel timed with CUDA events on the stream it runs on, after a warm-up
+    launch; the best of `repeats` launches."""
+    import torch
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream()
+    L = load()
+    check(L.osb_fp64_rate_probe(out.data_ptr(), blocks, iters, st.cuda_stream), "osb_fp64_rate_probe")
+    best = None
+    for _ in range(repeats):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        check(L.osb_fp64_rate_probe(out.data_ptr(), blocks, iters, st.cuda_stream), "osb_fp64_rate_probe")
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    flops = blocks * 256 * 8 * 16 * iters * 2
+    return {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "blocks": blocks, "iters": iters,
+            "flops": flops}
