@@ -31,7 +31,8 @@ struct osb_grid {
     int cur;  // which FP64 accumulator holds Q^n
     int qc;   // FP32 path: which stage register holds the FP32 copy of Q^n
     int copy_valid;
-    int zmarch;  // FP32 path kernels: 1 z-march (default), 0 three-kernel (OSB_FP32_STAGE=split3)
+    int zmarch;  // FP32 path kernels: 2 fused stage (orders 2, 4), 1 two z-march kernels, 0 three-kernel
+                 // (OSB_FP32_STAGE=fused|zmarch|split3 selects among those that apply)
     double t;
     long long step;
     double *U[2];
@@ -55,6 +56,7 @@ struct osb_grid {
     osb_closure *closure;     // learned correction added to R in every stage, or nullptr
     // FP32 z-march stage: TMA descriptors per stage source q[b] (b = 0, 1)
     zm::ZTma *ztma;           // [2 sources][flux, rhs]
+    fz::FTma *ftma;           // fused FP32 stage: descriptors per stage source q[b], or nullptr
     int *kerr;                // device error word of bounded in-kernel waits
     cudaGraphExec_t step_graph[2];  // one RK3 step starting with Q^n in U[0] / U[1]
     // per-step diagnostics series (osb_set_diag_series): block records of the
@@ -242,6 +244,43 @@ void build_ztma(osb_grid *g) {
         return;
     }
     g->ztma = t;
+}
+
+// TMA descriptors of the fused FP32 stage for both stage sources q[0], q[1]:
+// haloed plane boxes of 40 x (8 + 4R) points.  Left unused (cp.async loads)
+// when the x extent is not a multiple of 4 or OSB_FP32_LOADS=cpasync.
+void build_ftma(osb_grid *g) {
+    g->ftma = nullptr;
+    if (g->desc.precision != OSB_FP32 || g->desc.order > 4 || g->d.nx % 4) return;
+    const char *env = getenv("OSB_FP32_LOADS");
+    if (env && strcmp(env, "cpasync") == 0) return;
+    fz::FTma *t = new (std::nothrow) fz::FTma[2];
+    if (!t) return;
+    memset(t, 0, 2 * sizeof(fz::FTma));
+    const int eh = 8 + 4 * (g->desc.order / 2);
+    bool ok = true;
+    for (int b = 0; b < 2; ++b) {
+        const float *q = (const float *)g->q[b];
+        for (int f = 0; f < 5; ++f) ok = ok && encode_plane_map(&t[b].q[f], q + f * g->q_stride, g->d, 40, eh);
+        t[b].use = 1;
+    }
+    if (!ok) {
+        delete[] t;
+        return;
+    }
+    g->ftma = t;
+}
+
+// FP32 stage kernels of a grid: the fused stage where it applies (orders 2
+// and 4, viscous form A, periodic), else the two z-march kernels; the
+// environment can ask for the two-kernel or the three-kernel stage.
+int fp32_stage_mode(const osb_grid *g, int sym) {
+    const char *env = getenv("OSB_FP32_STAGE");
+    if (env && strcmp(env, "split3") == 0) return 0;
+    if (sym) return 0;
+    const bool fusable = g->desc.precision == OSB_FP32 && g->desc.visc_form == OSB_VISC_A && g->desc.order <= 4;
+    if (env && strcmp(env, "zmarch") == 0) return 1;
+    return fusable ? 2 : 1;
 }
 
 StageArgs base_args(const osb_grid *g) {
@@ -441,11 +480,9 @@ osb_status osb_grid_create(const osb_grid_desc *desc, const osb_params *prm, voi
         return cuda_fail(cudaErrorInvalidValue, "grid create: error word reset");
     }
     build_ztma(g);
+    build_ftma(g);
     g->cur = 0;
-    {
-        const char *env = getenv("OSB_FP32_STAGE");
-        g->zmarch = !(env && strcmp(env, "split3") == 0);
-    }
+    g->zmarch = fp32_stage_mode(g, 0);
     *out = g;
     return OSB_OK;
 }
@@ -469,6 +506,7 @@ osb_status osb_grid_destroy(osb_grid *g) {
     for (int b = 0; b < 2; ++b)
         if (g->step_graph[b]) cudaGraphExecDestroy(g->step_graph[b]);
     delete[] g->ztma;
+    delete[] g->ftma;
     delete g->batch_rec_host;
     delete g;
     return OSB_OK;
@@ -660,6 +698,51 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
     return a;
 }
 
+// The fused FP32 stage (fused.cuh) keeps the FP64 accumulator out of stages
+// 1 and 2: with Uf = q[qc] the FP32 copy of U[cur] and d the FP32 increment
+// (workspace fields 0..4),
+//   stage 1: src Uf;  q[1-qc] = Uf + alpha_1 dt R;  d = beta_1 dt R
+//   stage 2: src q[1-qc];  q[qc] = Uf + (d + alpha_2 dt R) (in place: Uf is
+//            only read at the point);  d += beta_2 dt R
+//   stage 3: src q[qc];  U[1-cur] = U[cur] + (double)(d + beta_3 dt R);
+//            q[1-qc] = float(U[1-cur])
+// which leaves the same registers as the other FP32 stages after a step.
+static bool use_fused(const osb_grid *g) { return g->zmarch == 2; }
+
+static StageArgs stage_args_fused(const osb_grid *g, int cur, int k) {
+    StageArgs a = stage_args(g, cur, k);
+    const int qc = cur;
+    a.fz_dinc = (float *)g->aux;
+    a.fz_dstride = g->aux_stride;
+    a.fz_mode = k + 1;
+    a.fz_has_d = 1;
+    a.fz_ufc = nullptr;
+    a.U_in = g->U[cur];
+    a.U_out = g->U[1 - cur];
+    a.u32_out = nullptr;
+    a.ztma_flux = a.ztma_rhs = nullptr;
+    if (k == 0) {
+        a.src = g->q[qc];
+        a.q_out = g->q[1 - qc];
+    } else if (k == 1) {
+        a.src = g->q[1 - qc];
+        a.fz_ufc = (const float *)g->q[qc];
+        a.q_out = g->q[qc];
+    } else {
+        a.src = g->q[qc];
+        a.q_out = nullptr;
+        a.u32_out = g->q[1 - qc];
+    }
+    a.src_stride = g->q_stride;
+    a.fz_tma = g->ftma ? (const void *)&g->ftma[(a.src == g->q[0]) ? 0 : 1] : nullptr;
+    return a;
+}
+
+// Arguments of stage k of a per-grid RK3 step.
+static StageArgs step_stage_args(const osb_grid *g, int cur, int k) {
+    return use_fused(g) ? stage_args_fused(g, cur, k) : stage_args(g, cur, k);
+}
+
 static osb_status ensure_stage_copy(osb_grid *g) {
     if (g->desc.precision == OSB_FP64 || g->copy_valid) return OSB_OK;
     cudaError_t e = g->desc.precision == OSB_FP32
@@ -681,7 +764,7 @@ static osb_status rk3_one_step(osb_grid *g) {
     osb_status s0 = ensure_stage_copy(g);
     if (s0 != OSB_OK) return s0;
     for (int k = 0; k < 3; ++k) {
-        StageArgs a = stage_args(g, g->cur, k);
+        StageArgs a = step_stage_args(g, g->cur, k);
         if (g->closure) {
             cudaError_t e = cl::closure_correction(g->closure, a.src, a.src_is_f64, a.src_stride, &a.closure);
             if (e != cudaSuccess) return cuda_fail(e, "closure correction");
@@ -722,7 +805,7 @@ static osb_status step_graph(osb_grid *g, int cur, cudaGraphExec_t *out) {
     if (e != cudaSuccess) return cuda_fail(e, "step capture begin");
     cudaError_t el = cudaSuccess;
     for (int k = 0; k < 3 && el == cudaSuccess; ++k) {
-        StageArgs a = stage_args(g, cur, k);
+        StageArgs a = step_stage_args(g, cur, k);
         a.stream = g->capture_st;
         el = g->K.stage(a);
         if (k == 0 && el == cudaSuccess) el = series_append(g, g->capture_st);
@@ -777,9 +860,16 @@ osb_status osb_euler_step(osb_grid *g, int nsteps) {
     for (int s = 0; s < nsteps; ++s) {
         osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;
-        StageArgs a = stage_args(g, g->cur, 0);
+        StageArgs a = use_fused(g) ? stage_args_fused(g, g->cur, 2) : stage_args(g, g->cur, 0);
         a.alpha_dt = a.beta_dt = g->prm.dt;
         a.q_out = nullptr;
+        if (use_fused(g)) {
+            // one stage of the fused kernel's final form, without an increment
+            a.src = g->q[g->qc];
+            a.fz_has_d = 0;
+            a.diag_rec = g->series ? g->diag_rec : nullptr;
+            a.fz_tma = g->ftma ? (const void *)&g->ftma[g->qc] : nullptr;
+        }
         if (g->desc.precision != OSB_FP64) a.u32_out = g->q[1 - g->qc];
         if (g->closure) {
             cudaError_t e = cl::closure_correction(g->closure, a.src, a.src_is_f64, a.src_stride, &a.closure);
@@ -1097,8 +1187,7 @@ osb_status osb_set_boundaries(osb_grid *g, int bc_x, int bc_y, int bc_z) {
     g->K = K;
     // the FP32 z-march kernels wrap periodically; symmetric grids take the
     // three-kernel stage
-    const char *env = getenv("OSB_FP32_STAGE");
-    g->zmarch = !sym && !(env && strcmp(env, "split3") == 0);
+    g->zmarch = fp32_stage_mode(g, sym);
     return OSB_OK;
 }
 

@@ -127,6 +127,14 @@ struct StageArgs {
     // block; layout: [0] = number of block records, [2 + 2b], [3 + 2b] = the
     // two sums of block b
     double *diag_rec;
+    // FP32 fused stage (one kernel per stage, orders 2 and 4): 0 = not used,
+    // 1..3 = RK stage of the increment form, forward Euler = 3 without fz_has_d
+    int fz_mode;
+    float *fz_dinc;         // FP32 increments d (5 fields, fz_dstride)
+    size_t fz_dstride;
+    const float *fz_ufc;    // stage 2: FP32 copy of U at the step start (q_stride)
+    int fz_has_d;           // stage 3: read d (0: forward Euler)
+    const void *fz_tma;     // host: TMA descriptors of the stencil source, or nullptr
 };
 
 
@@ -163,6 +171,18 @@ struct ZTma {
     int use;
 };
 }  // namespace zm
+
+namespace fz {
+// TMA descriptors of the fused stage: haloed plane boxes (40 x (8 + 4R) x 1)
+// of the five fields of one stencil source.
+struct FTma {
+    CUtensorMap q[5];
+    int use;
+};
+// The fused FP32 stage of radius 1 and 2 (fused_o2.cu, fused_o4.cu).
+cudaError_t launch_fused_r1(const StageArgs &a);
+cudaError_t launch_fused_r2(const StageArgs &a);
+}  // namespace fz
 
 // Persistent ensemble kernel (batch.cu).
 constexpr int MAXB = 128;  // instances per batch

@@ -672,10 +672,14 @@ cudaError_t launch_zstage(const StageArgs &a) {
 
 }  // namespace zm
 
-// Per-order stage entry: the z-march kernels for the FP32 path (form A,
-// orders <= 8), the three-kernel stage otherwise.
+// Per-order stage entry: the fused stage kernel (FP32 increment form, orders
+// 2 and 4) when the stage arguments ask for it, the two z-march kernels for
+// the FP32 path (form A, orders <= 8), the three-kernel stage otherwise.
 template <int R>
 cudaError_t stage_entry_z(const StageArgs &a) {
+    if constexpr (R <= 2) {
+        if (a.fz_mode) return R == 1 ? fz::launch_fused_r1(a) : fz::launch_fused_r2(a);
+    }
     if constexpr (R <= 4) {
         if (a.precision == OSB_FP32 && a.visc_form == OSB_VISC_A && !a.src_is_f64 && a.zmarch)
             return zm::launch_zstage<R>(a);

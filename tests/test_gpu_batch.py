@@ -89,10 +89,11 @@ def test_batch_fp32_close_to_oracle(osb, order):
             assert np.linalg.norm((Q[m] - Qo[m]).ravel()) / scale < 1e-5
 
 
-def test_batch_fp32_zmarch_items_match_per_grid_steps(osb):
+def test_batch_fp32_zmarch_items_match_per_grid_steps(osb, monkeypatch):
     """FP32 ensembles whose x extents are multiples of 4 run z-march items in
     the persistent kernel; per point they do the arithmetic of the per-grid
     z-march stage (ragged x and y tiles included)."""
+    monkeypatch.setenv("OSB_FP32_STAGE", "zmarch")
     specs = [(20, 1600.0, 0.1, 2e-3), (36, 400.0, 0.2, 1.5e-3), (12, 3000.0, 0.05, 3e-3), (32, 100.0, 0.3, 1e-3)]
     for order in (2, 4, 6, 8):
         a = _ensemble(osb, specs, osb.OSB_FP32, order=order, seed=31)
@@ -106,10 +107,11 @@ def test_batch_fp32_zmarch_items_match_per_grid_steps(osb):
             assert gb.diagnostics()["step"] == 5
 
 
-def test_batch_fp32_zmarch_items_with_tma_tiles(osb):
+def test_batch_fp32_zmarch_items_with_tma_tiles(osb, monkeypatch):
     """Grids wide enough for interior tiles (x >= 72, y >= 18): the persistent
     kernel loads their planes with TMA boxes whose descriptors live in the
     device record; results agree with per-grid stepping and the oracle."""
+    monkeypatch.setenv("OSB_FP32_STAGE", "zmarch")
     specs = [(72, 24, 16), (104, 32, 12)]
     grids, refs = [], []
     for i, (nx, ny, nz) in enumerate(specs):
@@ -131,6 +133,38 @@ def test_batch_fp32_zmarch_items_with_tma_tiles(osb):
         for m in range(5):
             scale = mnorm if 1 <= m <= 3 else np.linalg.norm(Qo[m].ravel())
             assert np.linalg.norm((Q[m] - Qo[m]).ravel()) / scale < 1e-5
+
+
+def test_batch_steps_mix_with_fused_per_grid_steps(osb):
+    """Per-grid FP32 steps of orders 2 and 4 run the fused stage, whose
+    stage registers differ from the ensemble's z-march items only inside a
+    step: steps of either kind may follow each other on the same grids.  The
+    mixed sequence agrees with per-grid steps to FP32 rounding of the stage
+    residuals, and with the oracle within the FP32 bound."""
+    specs = [(24, 800.0, 0.15, 2e-3), (32, 1600.0, 0.1, 1e-3)]
+    for order in (2, 4):
+        a = _ensemble(osb, specs, osb.OSB_FP32, order=order, seed=61)
+        b = _ensemble(osb, specs, osb.OSB_FP32, order=order, seed=61)
+        for g in a:
+            g.step(6)
+        for g in b:
+            g.step(2)
+        osb.batch_step(b, 2)
+        for g in b:
+            g.step(2)
+        for i, (ga, gb) in enumerate(zip(a, b)):
+            A, B = ga.get_state(), gb.get_state()
+            mnorm = np.linalg.norm(A[1:4].ravel())
+            for m in range(5):
+                scale = mnorm if 1 <= m <= 3 else np.linalg.norm(A[m].ravel())
+                assert np.linalg.norm((A[m] - B[m]).ravel()) / scale < 2e-6, (order, i, m)
+            n, Re, M, dt = specs[i]
+            case = orc.Case(n, n, n, order=order, Re=Re, Mach=M, dt=dt)
+            Qo = orc.rk3_step(case, orc.tgv_init(case, inputs.gaussian_noise(n, n, n, 61 + i), 1e-3), 6)
+            mo = np.linalg.norm(Qo[1:4].ravel())
+            for m in range(5):
+                scale = mo if 1 <= m <= 3 else np.linalg.norm(Qo[m].ravel())
+                assert np.linalg.norm((B[m] - Qo[m]).ravel()) / scale < 1e-5, (order, i, m)
 
 
 def test_batch_fp32_unaligned_extent_uses_point_items(osb):

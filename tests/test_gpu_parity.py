@@ -322,7 +322,56 @@ def test_fp32_zmarch_agrees_with_three_kernel_stage(osb, order, monkeypatch):
         assert err < 2e-6, (m, err)
 
 
-@pytest.mark.parametrize("dims,order", [((128, 24, 40), 4), ((104, 32, 20), 8), ((112, 40, 12), 6)])
+@pytest.mark.parametrize("dims,order", [((40, 40, 40), 4), ((72, 20, 30), 4), ((37, 20, 9), 2), ((64, 24, 17), 2),
+                                        ((70, 9, 33), 4), ((6, 5, 3), 4)])
+def test_fp32_fused_stage_agrees_with_two_and_three_kernel_stages(osb, dims, order, monkeypatch):
+    """The fused FP32 stage (one kernel per RK stage, FP32 increments in stages
+    1-2 and one FP64 accumulation per step) evaluates the same discrete
+    operator as the two z-march kernels and the three-kernel stage: after five
+    steps the states differ by FP32 rounding only.  Ragged tiles, odd and
+    non-multiple-of-4 x extents (scalar and 4-byte loads) and a grid smaller
+    than the stencil in every direction are included."""
+    nx, ny, nz = dims
+    noise = inputs.gaussian_noise(nx, ny, nz, seed=5)
+    out = {}
+    for mode in ("fused", "zmarch", "split3"):
+        monkeypatch.setenv("OSB_FP32_STAGE", mode)
+        g = _grid(osb, nx, ny, nz, order=order, precision=osb.OSB_FP32)
+        g.init_taylor_green(noise, 1e-3)
+        g.step(5)
+        out[mode] = g.get_state()
+        assert g.diagnostics()["nonfinite"] == 0
+    for other in ("zmarch", "split3"):
+        for m, err in enumerate(_fp32_err(out["fused"], out[other])):
+            assert err < 2e-6, (other, m, err)
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_fp32_fused_stage_independent_of_work_split(osb, order, monkeypatch):
+    """The fused stage's CTAs each march a contiguous run of the (tile, z)
+    planes, restarting with warm-up planes wherever a run enters a new tile.
+    Every output point sees the same operands, summed in the same order, however
+    the runs fall, so one CTA (every tile in turn), seven CTAs (runs that cross
+    tile boundaries mid-column) and the default split give the same state bit
+    for bit."""
+    nx, ny, nz = 64, 16, 23
+    noise = inputs.gaussian_noise(nx, ny, nz, seed=9)
+    outs = []
+    for ctas in ("1", "7", None):
+        if ctas is None:
+            monkeypatch.delenv("OSB_FUSED_CTAS", raising=False)
+        else:
+            monkeypatch.setenv("OSB_FUSED_CTAS", ctas)
+        g = _grid(osb, nx, ny, nz, order=order, precision=osb.OSB_FP32, dt=2e-3)
+        g.init_taylor_green(noise, 1e-2)
+        g.step(3)
+        outs.append(g.get_state())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("dims,order", [((128, 24, 40), 4), ((104, 32, 20), 8), ((112, 40, 12), 6),
+                                        ((96, 40, 20), 2)])
 def test_fp32_tma_and_cpasync_loads_are_bitwise_equal(osb, dims, order, monkeypatch):
     """Grids wide enough for interior tiles: those load planes with TMA boxes,
     boundary tiles with wrapped cp.async copies.  Both fill shared memory with
