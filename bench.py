@@ -82,6 +82,14 @@ def stage_flops_per_point(r: int) -> dict:
 
 
 ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}  # fused minimum per point-stage
+# Bytes the FP32 stage kernels move by design: the fused stage (orders 2, 4)
+# keeps the FP64 accumulator out of stages 1-2 (300 B per step); the two z-march
+# kernels (orders 6, 8) move 195 B per point-stage.
+DESIGN_BYTES_FP32 = {"fused": 100.0, "zmarch": 195.0}
+
+
+def fp32_kernel(order: int) -> str:
+    return "k_fused" if order <= 4 else "k_zrhs"
 
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # launch list of the same workload (profiles/launches_tgv256_o4_*.md).
@@ -89,7 +97,7 @@ ALG_BYTES = {"fp64": 400.0 / 3.0, "fp32": 320.0 / 3.0}  # fused minimum per poin
 # name bench.py reports.
 TRAFFIC_PER_LAUNCH = {
     ("tgv_256^3_order4_fp64", "k_resid"): 4.6204e9,  # profiles/launches_tgv256_o4_fp64.md
-    ("tgv_256^3_order4_fp32", "k_zrhs"): 2.4778e9,   # profiles/launches_tgv256_o4_fp32.md
+    ("tgv_256^3_order8_fp32", "k_zrhs"): None,
 }
 
 # FP64 peak from unit counts and clocks: 2 DFMA thread-instructions per SM per
@@ -407,11 +415,15 @@ def run_ours(args):
                 "peak_src": "FP64 FMA rate from unit counts and clock: 2 DFMA/SM/cycle x 2 flops x 152 SMs x 2070 MHz",
                 "flops_per_point": fl["resid"]}
     else:
+        kname = fp32_kernel(w["order"])
         achieved = ALG_BYTES["fp32"] * npts / (avg_ms * 1e-3) / 1e9
-        roof = {"kernel": "k_zrhs", "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
+        design = DESIGN_BYTES_FP32["fused" if kname == "k_fused" else "zmarch"]
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
-                "traffic": TRAFFIC_PER_LAUNCH.get((w["workload"], "k_zrhs")),
-                "peak_src": pk["src"]}
+                "traffic": TRAFFIC_PER_LAUNCH.get((w["workload"], kname)),
+                "peak_src": pk["src"],
+                "design_bytes_per_point_stage": design,
+                "design_bytes_gbs": design * npts / (avg_ms * 1e-3) / 1e9}
     if w["precision"] == "fp64":
         # the same kernel against the FP64 rate measured by the probe kernel
         meas = osb.fp64_rate()

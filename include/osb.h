@@ -271,6 +271,68 @@ osb_status osb_autotune(osb_grid *grid, int trial_steps, int *best_tz);
 osb_status osb_diagnostics_noalloc(const double *Q_dev, int nx, int ny, int nz, int order,
                                    const osb_params *params, double *out_dev, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * z-slab domain decomposition.  The paper runs its largest Taylor-Green case
+ * (Section 3.3) with the box split over many processes, the periodic
+ * boundaries and the subdomain faces kept up to date by halo transfers
+ * (Section 2.6).  Here one grid holds a slab of consecutive z planes of a
+ * periodic box; the caller moves the halo planes between slabs (on one GPU by
+ * device copies, across GPUs e.g. by NCCL send/recv) through staging buffers
+ * it owns, and advances the slabs one RK stage at a time:
+ *
+ *     for each step, for k = 0, 1, 2:
+ *         every slab: osb_halo_pack(slab, k, send_lo, send_hi)
+ *         exchange:   slab s receives recv_lo = send_hi of slab s-1 and
+ *                     recv_hi = send_lo of slab s+1 (periodic in s)
+ *         every slab: osb_halo_unpack(slab, k, recv_lo, recv_hi)
+ *         every slab: osb_rk3_stage(slab, k)
+ *
+ * A slab's array has nz = n_own + 2H planes: H = order ghost planes at each
+ * end (the nested first derivatives of viscous form A reach 2R = order planes)
+ * around the n_own planes it owns.  Each owned plane then evolves exactly as
+ * in the undivided box (bit for bit: the same operands in the same order).
+ * ------------------------------------------------------------------------ */
+
+/* Makes a grid a z-slab of a periodic box of nz_domain planes along z (the z
+ * spacing is 2 pi / nz_domain).  Requires nz >= 3 * order (two ghost widths
+ * and one owned width), a periodic z axis, no diagnostics series and no
+ * closure; osb_rk3_step, osb_euler_step and osb_batch_step then refuse the
+ * grid (OSB_ERR_UNSUPPORTED), osb_diagnostics reduces the owned planes only
+ * (means over those planes: combine slabs weighted by n_own, after exchanging
+ * source 3).  The grid's state is read and written with osb_set_state /
+ * osb_get_state as before, ghost planes included. */
+osb_status osb_set_z_slab(osb_grid *grid, int nz_domain);
+
+/* Bytes of one staging buffer (send_lo, send_hi, recv_lo or recv_hi) of a
+ * z-slab grid: 5 fields x order planes x nx x ny x 8 bytes (large enough for
+ * every source); 0 if the grid is not a slab. */
+size_t osb_halo_bytes(const osb_grid *grid);
+
+/* Packs the order planes next to each face of the slab's owned planes of one
+ * source into two staging buffers, layout [field][plane][y][x] in the source's
+ * element type (FP64, FP32 or double-float), contiguous:
+ *   source 0..2: the stencil source of RK stage `source` of the step in
+ *                progress (must equal the next stage osb_rk3_stage runs);
+ *   source 3:    the FP64 accumulator holding Q^n (before osb_diagnostics).
+ *  send_lo_dev / send_hi_dev: device, osb_halo_bytes bytes each, caller-owned,
+ *   8-byte aligned; written with the planes next to the low / high z face.
+ * Queued on the grid's stream (no synchronisation).  Errors: NULL arguments, a
+ * grid that is not a slab, a source out of order -> OSB_ERR_INVALID_ARG;
+ * unaligned buffers -> OSB_ERR_BUFFER; a failed launch -> OSB_ERR_CUDA. */
+osb_status osb_halo_pack(osb_grid *grid, int source, void *send_lo_dev, void *send_hi_dev);
+
+/* Unpacks the buffers received from the z neighbours into the ghost planes of
+ * the same source: recv_lo_dev (the low neighbour's send_hi) into the order
+ * planes below the owned planes, recv_hi_dev (the high neighbour's send_lo)
+ * into those above.  Same arguments, ownership and errors as osb_halo_pack. */
+osb_status osb_halo_unpack(osb_grid *grid, int source, const void *recv_lo_dev, const void *recv_hi_dev);
+
+/* One stage k (0, 1, 2, in this order) of the RK3 step (Section 2.4) on the
+ * grid's stream; after stage 2 the step is complete (time and step count
+ * advance).  Any grid can be stepped this way; a z-slab must be.  Errors: a
+ * stage out of order -> OSB_ERR_INVALID_ARG; a failed launch -> OSB_ERR_CUDA. */
+osb_status osb_rk3_stage(osb_grid *grid, int k);
+
 /* Measurement utility (no counterpart in the paper): the FP64 fused
  * multiply-add rate of the device, the roofline denominator of the FP64 stage
  * kernels.  One launch of `blocks` blocks of 256 threads; each thread runs 8

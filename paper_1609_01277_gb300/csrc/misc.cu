@@ -181,20 +181,23 @@ __device__ __forceinline__ double vel_d1(const double *__restrict__ rho, const d
     return s;
 }
 
+// Planes [zlo, zhi) of the array are reduced (a z-slab's own planes); nzd is
+// the number of planes of the whole periodic box along z (its spacing).
 template <int R>
 __global__ void __launch_bounds__(DIAG_THREADS)
     k_diag(const Dims d, const Phys ph, const Coef<double> c, double dt, const double *__restrict__ U,
-           size_t s, double *__restrict__ partials) {
+           size_t s, double *__restrict__ partials, int zlo, int zhi, int nzd) {
     double v[NDIAG];
 #pragma unroll
     for (int q = 0; q < NDIAG; ++q) v[q] = 0.0;
     const double two_pi = 6.283185307179586476925286766559, pi = 0.5 * two_pi;
     const double ih[3] = {d.nx / ((d.sym & 1) ? pi : two_pi), d.ny / ((d.sym & 2) ? pi : two_pi),
-                          d.nz / ((d.sym & 4) ? pi : two_pi)};
+                          nzd / ((d.sym & 4) ? pi : two_pi)};
     const double *rho = U, *m0 = U + s, *m1 = U + 2 * s, *m2 = U + 3 * s, *e = U + 4 * s;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < d.n;
+    const long long plane = (long long)d.nx * d.ny, i_end = zhi * plane;
+    for (long long i = zlo * plane + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < i_end;
          i += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(i % d.nx), y = (int)((i / d.nx) % d.ny), z = (int)(i / ((long long)d.nx * d.ny));
+        const int x = (int)(i % d.nx), y = (int)((i / d.nx) % d.ny), z = (int)(i / plane);
         const double r = rho[i];
         const double u0 = m0[i] / r, u1 = m1[i] / r, u2 = m2[i] / r;
         const double uu = u0 * u0 + u1 * u1 + u2 * u2;
@@ -255,19 +258,68 @@ __global__ void __launch_bounds__(DIAG_THREADS)
 
 cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const Coef<double> &c, double dt,
                                const double *U, size_t stride, double *partials, int max_partials,
-                               double *result, cudaStream_t st) {
+                               double *result, cudaStream_t st, int zlo, int zhi, int nzd) {
     const int blocks = diag_num_partials(d);
     if (blocks > max_partials) return cudaErrorInvalidValue;
+    if (zhi < 0) zhi = d.nz;
+    if (nzd <= 0) nzd = d.nz;
+    if (zlo < 0 || zhi > d.nz || zlo >= zhi) return cudaErrorInvalidValue;
     switch (order / 2) {
-        case 1: k_diag<1><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
-        case 2: k_diag<2><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
-        case 3: k_diag<3><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
-        case 4: k_diag<4><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
-        case 5: k_diag<5><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
-        case 6: k_diag<6><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials); break;
+        case 1: k_diag<1><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials, zlo, zhi, nzd); break;
+        case 2: k_diag<2><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials, zlo, zhi, nzd); break;
+        case 3: k_diag<3><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials, zlo, zhi, nzd); break;
+        case 4: k_diag<4><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials, zlo, zhi, nzd); break;
+        case 5: k_diag<5><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials, zlo, zhi, nzd); break;
+        case 6: k_diag<6><<<blocks, DIAG_THREADS, 0, st>>>(d, ph, c, dt, U, stride, partials, zlo, zhi, nzd); break;
         default: return cudaErrorInvalidValue;
     }
-    k_diag_final<<<1, DIAG_THREADS, 0, st>>>(partials, blocks, 1.0 / (double)d.n, result);
+    const double n = (double)(zhi - zlo) * d.nx * d.ny;
+    k_diag_final<<<1, DIAG_THREADS, 0, st>>>(partials, blocks, 1.0 / n, result);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// z-slab halo exchange (the decomposition of a periodic box into slabs of
+// planes, one per GPU): the H planes next to each face of a slab's own planes
+// are packed into two contiguous staging buffers, [field][plane][y][x], and
+// the buffers received from the neighbours are unpacked into the H ghost
+// planes at each end of the slab array.  Words of 4 or 8 bytes.
+// ---------------------------------------------------------------------------
+template <typename W>
+__global__ void k_halo(W *__restrict__ field, size_t stride, int nz, int H, long long plane, W *__restrict__ lo,
+                       W *__restrict__ hi, int unpack) {
+    const long long per = (long long)H * plane;  // words per field and face
+    const long long total = 2 * 5 * per;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int face = (int)(i / (5 * per));
+        const long long r = i - face * 5 * per;
+        const int m = (int)(r / per);
+        const long long j = r - m * per;
+        // own planes next to the face (pack) or the ghost planes beyond it (unpack)
+        const long long z0 = unpack ? (face ? (long long)(nz - H) : 0) : (face ? (long long)(nz - 2 * H) : (long long)H);
+        W *f = field + m * stride + z0 * plane + j;
+        W *b = (face ? hi : lo) + m * per + j;
+        if (unpack)
+            *f = *b;
+        else
+            *b = *f;
+    }
+}
+
+cudaError_t launch_halo(void *field, size_t stride, int esize, int nz, int H, long long plane, void *lo, void *hi,
+                        int unpack, cudaStream_t st) {
+    const long long total = 2LL * 5 * H * plane;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (esize == 8)
+        k_halo<unsigned long long><<<(int)blocks, 256, 0, st>>>(static_cast<unsigned long long *>(field), stride, nz,
+                                                               H, plane, static_cast<unsigned long long *>(lo),
+                                                               static_cast<unsigned long long *>(hi), unpack);
+    else
+        k_halo<unsigned int><<<(int)blocks, 256, 0, st>>>(static_cast<unsigned int *>(field), stride, nz, H, plane,
+                                                         static_cast<unsigned int *>(lo),
+                                                         static_cast<unsigned int *>(hi), unpack);
     return cudaGetLastError();
 }
 

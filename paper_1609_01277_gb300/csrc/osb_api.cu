@@ -65,6 +65,12 @@ struct osb_grid {
     double *series;
     int series_cap;
     int *series_count;
+    // z-slab of a larger periodic box (osb_set_z_slab): planes of the whole box
+    // along z (0: not a slab), ghost planes at each end, next stage of
+    // osb_rk3_stage
+    int slab_nzd;
+    int slab_h;
+    int stage_pos;
 };
 
 namespace {
@@ -827,6 +833,8 @@ static osb_status step_graph(osb_grid *g, int cur, cudaGraphExec_t *out) {
 
 osb_status osb_rk3_step(osb_grid *g, int nsteps) {
     if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    if (g->slab_nzd) return fail(OSB_ERR_UNSUPPORTED, "z-slab grids step one stage at a time (osb_rk3_stage)");
+    if (g->stage_pos) return fail(OSB_ERR_INVALID_ARG, "a step begun with osb_rk3_stage is unfinished");
     const char *env = getenv("OSB_GRAPHS");
     const bool graphs = nsteps >= 2 && !g->closure && !g->prof_ev && !(env && strcmp(env, "0") == 0);
     if (graphs) {
@@ -857,6 +865,8 @@ osb_status osb_rk3_step(osb_grid *g, int nsteps) {
 // register; the FP32 path also writes the next step's FP32 stencil source.
 osb_status osb_euler_step(osb_grid *g, int nsteps) {
     if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    if (g->slab_nzd) return fail(OSB_ERR_UNSUPPORTED, "z-slab grids step one stage at a time (osb_rk3_stage)");
+    if (g->stage_pos) return fail(OSB_ERR_INVALID_ARG, "a step begun with osb_rk3_stage is unfinished");
     for (int s = 0; s < nsteps; ++s) {
         osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;
@@ -888,8 +898,9 @@ osb_status osb_euler_step(osb_grid *g, int nsteps) {
 
 osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
     if (!g || !out) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    const int zlo = g->slab_nzd ? g->slab_h : 0, zhi = g->slab_nzd ? g->d.nz - g->slab_h : -1;
     cudaError_t e = launch_diagnostics(g->d, g->ph, g->desc.order, g->c64, g->prm.dt, g->U[g->cur], g->u_stride,
-                                       g->partials, g->max_partials, g->result, g->st);
+                                       g->partials, g->max_partials, g->result, g->st, zlo, zhi, g->slab_nzd);
     if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
     double h[NDIAG];
     int herr = 0;
@@ -1120,13 +1131,19 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
 
 extern "C" {
 
-osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) { return batch_run(grids, n, nsteps); }
+osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) {
+    for (int i = 0; grids && i < n; ++i)
+        if (grids[i] && (grids[i]->slab_nzd || grids[i]->stage_pos))
+            return fail(OSB_ERR_UNSUPPORTED, "batch grids must be whole periodic boxes between steps");
+    return batch_run(grids, n, nsteps);
+}
 
 osb_status osb_grid_set_closure(osb_grid *g, osb_closure *c) {
     if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
     if (c && cl::closure_points(c) != g->d.n) return fail(OSB_ERR_INVALID_ARG, "closure grid size differs from the grid's");
     if (c && g->desc.precision == OSB_DF64) return fail(OSB_ERR_UNSUPPORTED, "closures take FP64 or FP32 grids");
     if (c && g->d.sym) return fail(OSB_ERR_UNSUPPORTED, "closures take periodic grids");
+    if (c && g->slab_nzd) return fail(OSB_ERR_UNSUPPORTED, "no closure on a z-slab");
     g->closure = c;
     return OSB_OK;
 }
@@ -1135,6 +1152,7 @@ osb_status osb_grid_set_closure(osb_grid *g, osb_closure *c) {
 // the state at the start of every step), fused into the first stage.
 osb_status osb_set_diag_series(osb_grid *g, double *series_dev, int capacity) {
     if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    if (series_dev && g->slab_nzd) return fail(OSB_ERR_UNSUPPORTED, "no diagnostics series on a z-slab");
     if (series_dev && (capacity < 1 || ((uintptr_t)series_dev & 7)))
         return fail(OSB_ERR_INVALID_ARG, "series: capacity >= 1 and an 8-byte aligned buffer");
     // captured step graphs hold the previous first-stage arguments
@@ -1165,6 +1183,7 @@ osb_status osb_diag_series_count(osb_grid *g, long long *count) {
 // [0, 2 pi), points at 2 pi i / n.
 osb_status osb_set_boundaries(osb_grid *g, int bc_x, int bc_y, int bc_z) {
     if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    if (g->slab_nzd) return fail(OSB_ERR_UNSUPPORTED, "z-slabs keep periodic boundaries");
     const int bc[3] = {bc_x, bc_y, bc_z};
     int sym = 0;
     for (int a = 0; a < 3; ++a) {
@@ -1264,3 +1283,103 @@ osb_status osb_autotune(osb_grid *g, int trial_steps, int *best_tz) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// z-slab decomposition (one slab of planes per GPU; halo planes exchanged by
+// the caller through staging buffers, e.g. with NCCL send/recv)
+// ---------------------------------------------------------------------------
+osb_status osb_set_z_slab(osb_grid *g, int nz_domain) {
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    const int H = g->desc.order;  // 2R planes: nested first derivatives of form A reach 2R planes
+    if (nz_domain < 1) return fail(OSB_ERR_INVALID_ARG, "nz_domain must be >= 1");
+    if (g->desc.nz < 3 * H) return fail(OSB_ERR_INVALID_ARG, "a slab needs nz >= 3 * order planes (2 * order ghosts)");
+    if (g->d.sym & 4) return fail(OSB_ERR_UNSUPPORTED, "z-slabs decompose a periodic z axis");
+    if (g->series || g->closure) return fail(OSB_ERR_UNSUPPORTED, "no diagnostics series or closure on a z-slab");
+    if (g->stage_pos) return fail(OSB_ERR_INVALID_ARG, "a step begun with osb_rk3_stage is unfinished");
+    for (int b = 0; b < 2; ++b)
+        if (g->step_graph[b]) {
+            cudaGraphExecDestroy(g->step_graph[b]);
+            g->step_graph[b] = nullptr;
+        }
+    g->slab_nzd = nz_domain;
+    g->slab_h = H;
+    make_coefs(g->desc.order, g->desc.nx, g->desc.ny, nz_domain, &g->c64, &g->c32, g->d.sym);
+    make_coefs_dd(g->c64, &g->cdd);
+    return OSB_OK;
+}
+
+size_t osb_halo_bytes(const osb_grid *g) {
+    if (!g || !g->slab_nzd) return 0;
+    return (size_t)5 * g->slab_h * g->desc.nx * g->desc.ny * 8;
+}
+
+// Stencil source of RK stage k (0..2) of the step in progress, or (k = 3) the
+// FP64 accumulator holding Q^n; its field stride and element size.
+static void halo_source(const osb_grid *g, int k, void **p, size_t *stride, int *esize) {
+    if (k == 3) {
+        *p = g->U[g->cur];
+        *stride = g->u_stride;
+        *esize = 8;
+        return;
+    }
+    const StageArgs a = step_stage_args(g, g->cur, k);
+    *p = const_cast<void *>(a.src);
+    *stride = a.src_stride;
+    *esize = a.src_is_f64 ? 8 : (int)tsize(&g->desc);
+}
+
+static osb_status halo_common(osb_grid *g, int source, void *lo, void *hi, int unpack) {
+    if (!g || !lo || !hi) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    if (!g->slab_nzd) return fail(OSB_ERR_INVALID_ARG, "not a z-slab (osb_set_z_slab)");
+    if (source < 0 || source > 3) return fail(OSB_ERR_INVALID_ARG, "source must be 0..2 (stage) or 3 (accumulator)");
+    if (source < 3 && source != g->stage_pos)
+        return fail(OSB_ERR_INVALID_ARG, "the source of a stage is exchanged right before that stage");
+    if (((uintptr_t)lo & 7) || ((uintptr_t)hi & 7)) return fail(OSB_ERR_BUFFER, "staging buffers must be 8-byte aligned");
+    if (source == 0) {
+        osb_status s0 = ensure_stage_copy(g);
+        if (s0 != OSB_OK) return s0;
+    }
+    void *f = nullptr;
+    size_t stride = 0;
+    int esize = 0;
+    halo_source(g, source, &f, &stride, &esize);
+    const cudaError_t e = launch_halo(f, stride, esize, g->d.nz, g->slab_h, (long long)g->d.nx * g->d.ny, lo, hi,
+                                      unpack, g->st);
+    if (e != cudaSuccess) return cuda_fail(e, unpack ? "halo unpack" : "halo pack");
+    return OSB_OK;
+}
+
+osb_status osb_halo_pack(osb_grid *g, int source, void *send_lo_dev, void *send_hi_dev) {
+    return halo_common(g, source, send_lo_dev, send_hi_dev, 0);
+}
+
+osb_status osb_halo_unpack(osb_grid *g, int source, const void *recv_lo_dev, const void *recv_hi_dev) {
+    return halo_common(g, source, const_cast<void *>(recv_lo_dev), const_cast<void *>(recv_hi_dev), 1);
+}
+
+osb_status osb_rk3_stage(osb_grid *g, int k) {
+    if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
+    if (k != g->stage_pos) return fail(OSB_ERR_INVALID_ARG, "stages run in order 0, 1, 2");
+    if (k == 0) {
+        osb_status s0 = ensure_stage_copy(g);
+        if (s0 != OSB_OK) return s0;
+    }
+    StageArgs a = step_stage_args(g, g->cur, k);
+    if (g->closure) {
+        cudaError_t e = cl::closure_correction(g->closure, a.src, a.src_is_f64, a.src_stride, &a.closure);
+        if (e != cudaSuccess) return cuda_fail(e, "closure correction");
+    }
+    cudaError_t e = g->K.stage(a);
+    if (e != cudaSuccess) return cuda_fail(e, "rk3 stage launch");
+    if (k == 0 && (e = series_append(g, g->st)) != cudaSuccess) return cuda_fail(e, "series launch");
+    if (k < 2) {
+        g->stage_pos = k + 1;
+        return OSB_OK;
+    }
+    g->stage_pos = 0;
+    g->cur = 1 - g->cur;
+    g->qc = g->cur;
+    g->step += 1;
+    g->t = g->step * g->prm.dt;
+    return OSB_OK;
+}

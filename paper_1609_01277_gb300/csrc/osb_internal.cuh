@@ -228,9 +228,17 @@ void set_last_error(const char *msg);
 // Misc kernels (init, diagnostics).
 cudaError_t launch_init_tgv(const Dims &d, const Phys &ph, double *U, size_t stride,
                             const double *noise, double amp, cudaStream_t st);
+// Diagnostics of planes [zlo, zhi) of the array (zhi < 0: all); nzd planes of
+// the whole box along z (0: the array's nz).
 cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const Coef<double> &c,
                                double dt, const double *U, size_t stride, double *partials,
-                               int max_partials, double *result, cudaStream_t st);
+                               int max_partials, double *result, cudaStream_t st, int zlo = 0, int zhi = -1,
+                               int nzd = 0);
+// z-slab halo: pack the H own planes next to each face of the array (nz
+// planes, H ghost planes at each end) into lo/hi, or unpack lo/hi into the
+// ghost planes; 5 fields of esize-byte words (4 or 8), field stride in words.
+cudaError_t launch_halo(void *field, size_t stride, int esize, int nz, int H, long long plane, void *lo, void *hi,
+                        int unpack, cudaStream_t st);
 int diag_num_partials(const Dims &d);
 cudaError_t launch_to_dd(const double *U, size_t u_stride, dd *q, size_t q_stride, int n, double e_ref,
                          cudaStream_t st);

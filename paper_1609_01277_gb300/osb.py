@@ -35,6 +35,7 @@ EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_gri
            "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
            "osb_box_filter", "osb_scalar_rk3", "osb_set_boundaries", "osb_set_diag_series",
            "osb_diag_series_count", "osb_profile_start", "osb_profile_stop", "osb_fp64_rate_probe",
+           "osb_set_z_slab", "osb_halo_bytes", "osb_halo_pack", "osb_halo_unpack", "osb_rk3_stage",
            "osb_status_string", "osb_last_error")
 KERNEL_KINDS = ("prim", "grad", "resid")
 
@@ -102,12 +103,18 @@ def load(path: str | None = None):
     L.osb_profile_start.argtypes = [vp, ctypes.c_int]
     L.osb_profile_stop.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
     L.osb_fp64_rate_probe.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp]
+    L.osb_set_z_slab.argtypes = [vp, ctypes.c_int]
+    L.osb_halo_bytes.argtypes = [vp]
+    L.osb_halo_bytes.restype = sz
+    L.osb_halo_pack.argtypes = [vp, ctypes.c_int, vp, vp]
+    L.osb_halo_unpack.argtypes = [vp, ctypes.c_int, vp, vp]
+    L.osb_rk3_stage.argtypes = [vp, ctypes.c_int]
     L.osb_status_string.argtypes = [ctypes.c_int]
     L.osb_status_string.restype = ctypes.c_char_p
     L.osb_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("osb_state_bytes", "osb_workspace_bytes", "osb_status_string", "osb_last_error",
-                        "osb_closure_param_count", "osb_closure_workspace_bytes"):
+                        "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_halo_bytes"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -235,6 +242,28 @@ class Grid:
 
     def step(self, nsteps: int = 1) -> None:
         check(load().osb_rk3_step(self.handle, int(nsteps)), "osb_rk3_step")
+
+    def stage(self, k: int) -> None:
+        """RK stage k (0, 1, 2 in order) of the step in progress."""
+        check(load().osb_rk3_stage(self.handle, int(k)), "osb_rk3_stage")
+
+    def set_z_slab(self, nz_domain: int) -> None:
+        """Make this grid a z-slab (ghost planes included in nz) of a periodic
+        box of nz_domain planes."""
+        check(load().osb_set_z_slab(self.handle, int(nz_domain)), "osb_set_z_slab")
+
+    def halo_bytes(self) -> int:
+        return int(load().osb_halo_bytes(self.handle))
+
+    def halo_pack(self, source: int, send_lo, send_hi) -> None:
+        """Pack the planes next to the slab faces of a source (0..2: stage
+        source, 3: accumulator) into two device buffers (torch tensors)."""
+        check(load().osb_halo_pack(self.handle, int(source), send_lo.data_ptr(), send_hi.data_ptr()),
+              "osb_halo_pack")
+
+    def halo_unpack(self, source: int, recv_lo, recv_hi) -> None:
+        check(load().osb_halo_unpack(self.handle, int(source), recv_lo.data_ptr(), recv_hi.data_ptr()),
+              "osb_halo_unpack")
 
     def euler_step(self, nsteps: int = 1) -> None:
         """Forward Euler steps (Section 2.4), mixable with step()."""

@@ -147,3 +147,13 @@ def test_scalar_rejects_bad_arguments_before_gpu_work(osb):
     assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 4, a, 0.1, 1e-3, -1, None) == 1
     assert L.osb_scalar_rk3(ok + 4, ok, None, 8, 8, 8, 4, a, 0.1, 1e-3, 1, None) == 6
     assert L.osb_scalar_rk3(ok, ok, None, 8, 8, 8, 4, a, 0.1, 1e-3, 0, None) == 0  # nothing to do
+
+
+
+def test_z_slab_calls_reject_null_grids(osb):
+    L = osb.load()
+    assert L.osb_set_z_slab(None, 64) == 1
+    assert L.osb_halo_bytes(None) == 0
+    assert L.osb_halo_pack(None, 0, 256, 512) == 1
+    assert L.osb_halo_unpack(None, 0, 256, 512) == 1
+    assert L.osb_rk3_stage(None, 0) == 1

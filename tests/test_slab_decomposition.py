@@ -35,15 +35,21 @@ def _free_port() -> int:
 
 
 def _exchange(q: np.ndarray, H: int) -> np.ndarray:
-    """Slab with H ghost planes on each side from the periodic z-neighbours."""
+    """Slab with H ghost planes on each side from the periodic z-neighbours:
+    each rank sends its first H planes to the rank below and its last H planes
+    to the rank above, and receives the matching faces (neighbour send/recv,
+    as NCCL would carry them between GPUs)."""
     import torch
     rank, world = dist.get_rank(), dist.get_world_size()
-    faces = torch.from_numpy(np.ascontiguousarray(np.concatenate([q[:, :H], q[:, -H:]], axis=1)))
-    got = [torch.empty_like(faces) for _ in range(world)]
-    dist.all_gather(got, faces)
-    below = got[(rank - 1) % world].numpy()[:, H:]   # last H planes of the rank below
-    above = got[(rank + 1) % world].numpy()[:, :H]   # first H planes of the rank above
-    return np.ascontiguousarray(np.concatenate([below, q, above], axis=1))
+    below_rank, above_rank = (rank - 1) % world, (rank + 1) % world
+    lo = torch.from_numpy(np.ascontiguousarray(q[:, :H]))
+    hi = torch.from_numpy(np.ascontiguousarray(q[:, -H:]))
+    below, above = torch.empty_like(hi), torch.empty_like(lo)
+    reqs = [dist.isend(lo, below_rank, tag=1), dist.isend(hi, above_rank, tag=2),
+            dist.irecv(below, below_rank, tag=2), dist.irecv(above, above_rank, tag=1)]
+    for r in reqs:
+        r.wait()
+    return np.ascontiguousarray(np.concatenate([below.numpy(), q, above.numpy()], axis=1))
 
 
 def _worker(rank: int, world: int, port: int, out_dir: str):
