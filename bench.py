@@ -97,7 +97,9 @@ def fp32_kernel(order: int) -> str:
 # name bench.py reports.
 TRAFFIC_PER_LAUNCH = {
     ("tgv_256^3_order4_fp64", "k_resid"): 4.6204e9,  # profiles/launches_tgv256_o4_fp64.md
-    ("tgv_256^3_order8_fp32", "k_zrhs"): None,
+    # average over the three stage launches, scaled from 192^3 by the points
+    # (profiles/k_fused_tgv192_o4_fp32.md)
+    ("tgv_256^3_order4_fp32", "k_fused"): 1.638e9,
 }
 
 # FP64 peak from unit counts and clocks: 2 DFMA thread-instructions per SM per

@@ -98,6 +98,7 @@ struct Geo {
 // them straight from the parameter bank.
 struct FArgs {
     Dims d;
+    int zchunk;                // z planes per segment
     float2 c1[3][MAXR + 1];    // c_k / h_a
     float2 nc1[3][MAXR + 1];   // -c_k / h_a (flux divergences, tap by tap)
     float2 d1ir[3][MAXR + 1];  // c_k / (h_a Re): the gradient in units of 1/Re
@@ -921,18 +922,21 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const __grid_constant__ FArgs a
 #pragma unroll
         for (int k = 0; k < 2 * R + 1; ++k) rg.q[f][k] = zero2();
     rg.ke = rg.ens = 0.0;
-    // this CTA's run of the (tile, z) planes in tile-major order; one march per
-    // tile the run touches (with its own 4R warm-up planes)
-    const int tiles_x = (d.nx + TX - 1) / TX;
-    const long long total = (long long)tiles_x * ((d.ny + TY - 1) / TY) * d.nz;
+    // Work: z chunks of a.zchunk planes of every tile, ordered tile-fastest then
+    // chunk, so that the CTAs resident at any time cover a narrow band of z
+    // planes whose haloed loads the L2 serves; CTA b takes the b-th of
+    // gridDim.x equal runs of that order, one march (with its 4R warm-up
+    // planes) per (tile, chunk) segment the run touches.
+    const int tiles_x = (d.nx + TX - 1) / TX, tiles = tiles_x * ((d.ny + TY - 1) / TY);
+    const int nchunk = (d.nz + a.zchunk - 1) / a.zchunk;
+    const long long total = (long long)tiles * nchunk;  // segments
     long long pos = total * blockIdx.x / gridDim.x;
     const long long stop = total * (blockIdx.x + 1) / gridDim.x;
 #pragma unroll 1
-    while (pos < stop) {
-        const int tile = (int)(pos / d.nz);
-        c.z0 = (int)(pos - (long long)tile * d.nz);
-        c.z1 = (int)min((long long)d.nz, c.z0 + (stop - pos));
-        pos += c.z1 - c.z0;
+    for (; pos < stop; ++pos) {
+        const int chunk = (int)(pos / tiles), tile = (int)(pos - (long long)chunk * tiles);
+        c.z0 = chunk * a.zchunk;
+        c.z1 = min(d.nz, c.z0 + a.zchunk);
         c.x0 = (tile % tiles_x) * TX;
         c.y0 = (tile / tiles_x) * TY;
         c.Lbeg = c.z0 - 2 * R;
@@ -973,18 +977,10 @@ constexpr size_t fused_smem() {
 }
 
 // Host: kernel arguments from the stage arguments, then one launch.
-// Resident CTAs of the fused kernel on the current device: two per SM (the
-// shared memory of a CTA leaves room for two).
-inline long long resident_ctas(size_t) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
-            sms = 152;
-    }
-    return 2LL * sms;
-}
+// z planes per segment: short enough that the resident CTAs cover a narrow
+// band of planes (L2 hits for the haloed loads), long enough to amortise the
+// 4R warm-up planes of a march.
+constexpr int FUSED_ZCHUNK = 32;
 
 template <int R>
 cudaError_t launch_fused(const StageArgs &s) {
@@ -1037,20 +1033,19 @@ cudaError_t launch_fused(const StageArgs &s) {
     a.us = s.u_stride;
     a.ds = s.fz_dstride;
     a.has_d = s.fz_has_d;
-    // persistent grid: twice as many CTAs as are resident at once (two per
-    // SM; the second round evens out CTAs that run slower, e.g. on tiles that
-    // wrap at the periodic boundary), each marching an equal run of the
-    // (tile, z) planes; small grids get fewer CTAs so that a run keeps at
-    // least 8 planes per 4R warm-up planes (measured at 256^3: one to eight
-    // rounds of CTAs within 10% of each other, two the fastest at order 4)
-    const long long planes = (long long)((s.d.nx + TX - 1) / TX) * ((s.d.ny + TY - 1) / TY) * s.d.nz;
-    long long ctas = 2 * resident_ctas(sm);
-    if (planes / ctas < 8) ctas = (planes + 7) / 8;
+    int zc = FUSED_ZCHUNK;
+    if (const char *env = getenv("OSB_FUSED_ZCHUNK")) {
+        const int v = atoi(env);
+        if (v >= 1) zc = v;
+    }
+    a.zchunk = zc;
+    const long long segs = (long long)((s.d.nx + TX - 1) / TX) * ((s.d.ny + TY - 1) / TY) * ((s.d.nz + zc - 1) / zc);
+    long long ctas = segs;  // one segment per CTA; the hardware hands segments to SMs in order
     if (const char *env = getenv("OSB_FUSED_CTAS")) {
         const long long v = atoll(env);
         if (v >= 1) ctas = v;
     }
-    if (ctas > planes) ctas = planes;
+    if (ctas > segs) ctas = segs;
     const dim3 grid((unsigned)ctas);
     static const FTma none = {};
     const FTma &tm = s.fz_tma ? *static_cast<const FTma *>(s.fz_tma) : none;
