@@ -67,7 +67,7 @@ def build(force: bool = False, jobs: int | None = None) -> str:
     with open(os.path.join(OUT, "ptxas.log"), "w") as f:
         f.write("\n".join(logs))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -12,9 +12,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "osb_internal.cuh"
 
 using namespace osb;
+
+namespace {
+// NVTX range around a library call or one of its phases: visible in Nsight
+// timelines when a tool is attached, a few nanoseconds otherwise.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+const char *const kStageRange[3] = {"osb rk3 stage 1", "osb rk3 stage 2", "osb rk3 stage 3"};
+}  // namespace
 
 struct osb_grid {
     osb_grid_desc desc;
@@ -767,9 +781,11 @@ static cudaError_t series_append(const osb_grid *g, cudaStream_t st) {
 }
 
 static osb_status rk3_one_step(osb_grid *g) {
+    NvtxRange step_range("osb rk3 step");
     osb_status s0 = ensure_stage_copy(g);
     if (s0 != OSB_OK) return s0;
     for (int k = 0; k < 3; ++k) {
+        NvtxRange stage_range(kStageRange[k]);
         StageArgs a = step_stage_args(g, g->cur, k);
         if (g->closure) {
             cudaError_t e = cl::closure_correction(g->closure, a.src, a.src_is_f64, a.src_stride, &a.closure);
@@ -833,6 +849,7 @@ static osb_status step_graph(osb_grid *g, int cur, cudaGraphExec_t *out) {
 
 osb_status osb_rk3_step(osb_grid *g, int nsteps) {
     if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    NvtxRange range("osb_rk3_step");
     if (g->slab_nzd) return fail(OSB_ERR_UNSUPPORTED, "z-slab grids step one stage at a time (osb_rk3_stage)");
     if (g->stage_pos) return fail(OSB_ERR_INVALID_ARG, "a step begun with osb_rk3_stage is unfinished");
     const char *env = getenv("OSB_GRAPHS");
@@ -841,6 +858,7 @@ osb_status osb_rk3_step(osb_grid *g, int nsteps) {
         osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;
         for (int s = 0; s < nsteps; ++s) {
+            NvtxRange step_range("osb rk3 step (graph replay)");
             cudaGraphExec_t ge = nullptr;
             osb_status st = step_graph(g, g->cur, &ge);
             if (st != OSB_OK) return st;
@@ -865,6 +883,7 @@ osb_status osb_rk3_step(osb_grid *g, int nsteps) {
 // register; the FP32 path also writes the next step's FP32 stencil source.
 osb_status osb_euler_step(osb_grid *g, int nsteps) {
     if (!g || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    NvtxRange range("osb_euler_step");
     if (g->slab_nzd) return fail(OSB_ERR_UNSUPPORTED, "z-slab grids step one stage at a time (osb_rk3_stage)");
     if (g->stage_pos) return fail(OSB_ERR_INVALID_ARG, "a step begun with osb_rk3_stage is unfinished");
     for (int s = 0; s < nsteps; ++s) {
@@ -898,6 +917,7 @@ osb_status osb_euler_step(osb_grid *g, int nsteps) {
 
 osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
     if (!g || !out) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    NvtxRange range("osb_diagnostics");
     const int zlo = g->slab_nzd ? g->slab_h : 0, zhi = g->slab_nzd ? g->d.nz - g->slab_h : -1;
     cudaError_t e = launch_diagnostics(g->d, g->ph, g->desc.order, g->c64, g->prm.dt, g->U[g->cur], g->u_stride,
                                        g->partials, g->max_partials, g->result, g->st, zlo, zhi, g->slab_nzd);
@@ -1132,6 +1152,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
 extern "C" {
 
 osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps) {
+    NvtxRange range("osb_batch_step");
     for (int i = 0; grids && i < n; ++i)
         if (grids[i] && (grids[i]->slab_nzd || grids[i]->stage_pos))
             return fail(OSB_ERR_UNSUPPORTED, "batch grids must be whole periodic boxes between steps");
@@ -1330,6 +1351,7 @@ static void halo_source(const osb_grid *g, int k, void **p, size_t *stride, int 
 
 static osb_status halo_common(osb_grid *g, int source, void *lo, void *hi, int unpack) {
     if (!g || !lo || !hi) return fail(OSB_ERR_INVALID_ARG, "NULL argument");
+    NvtxRange range(unpack ? "osb_halo_unpack" : "osb_halo_pack");
     if (!g->slab_nzd) return fail(OSB_ERR_INVALID_ARG, "not a z-slab (osb_set_z_slab)");
     if (source < 0 || source > 3) return fail(OSB_ERR_INVALID_ARG, "source must be 0..2 (stage) or 3 (accumulator)");
     if (source < 3 && source != g->stage_pos)
@@ -1360,6 +1382,7 @@ osb_status osb_halo_unpack(osb_grid *g, int source, const void *recv_lo_dev, con
 osb_status osb_rk3_stage(osb_grid *g, int k) {
     if (!g) return fail(OSB_ERR_INVALID_ARG, "grid is NULL");
     if (k != g->stage_pos) return fail(OSB_ERR_INVALID_ARG, "stages run in order 0, 1, 2");
+    NvtxRange range(kStageRange[k]);
     if (k == 0) {
         osb_status s0 = ensure_stage_copy(g);
         if (s0 != OSB_OK) return s0;

@@ -43,3 +43,25 @@ def test_compare_curves_reports_both_ke_errors():
     assert abs(r["ke_err_every_step"] - 1e-4 / 0.125) < 2e-5
     assert r["ke_err"] <= r["ke_err_every_step"] + 1e-15
     assert r["speedup"] == 1.0
+
+
+def test_series_csv_rows_and_dissipation(tmp_path):
+    """The CSV writer's columns on a series with a known decay rate."""
+    dt, Re = 0.01, 1600.0
+    t = np.arange(101) * dt
+    ke = 0.125 * np.exp(-0.5 * t)
+    ens = 0.2 + 0.1 * t
+    path = tmp_path / "series.csv"
+    ex.write_series_csv(str(path), ke, ens, dt, Re, step0=3)
+    lines = path.read_text().splitlines()
+    assert lines[0] == "step,t,ke,enstrophy,dissipation,visc_dissipation"
+    rows = np.array([[float(v) for v in line.split(",")] for line in lines[1:]])
+    assert rows.shape == (101, 6)
+    assert np.array_equal(rows[:, 0], np.arange(3, 104))
+    assert np.allclose(rows[:, 1], (3 + np.arange(101)) * dt, rtol=0, atol=1e-15)
+    assert np.array_equal(rows[:, 2], ke) and np.array_equal(rows[:, 3], ens)
+    assert np.max(np.abs(rows[1:-1, 4] - 0.0625 * np.exp(-0.5 * t[1:-1]))) < 1e-5
+    assert np.allclose(rows[:, 5], 2.0 * ens / Re, rtol=1e-15)
+    one = tmp_path / "one.csv"
+    ex.write_series_csv(str(one), ke[:1], ens[:1], dt, Re)
+    assert one.read_text().splitlines()[1].split(",")[4] == ""
