@@ -39,7 +39,10 @@ typedef enum {
     OSB_ERR_CUDA = 3,        /* a CUDA runtime call or a kernel launch failed   */
     OSB_ERR_NONFINITE = 4,   /* the state holds NaN or Inf                      */
     OSB_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up              */
-    OSB_ERR_BUFFER = 6       /* a buffer is too small or misaligned             */
+    OSB_ERR_BUFFER = 6,      /* a buffer is too small or misaligned             */
+    OSB_ERR_BOUNDS = 7       /* bounds-check build only: a kernel computed an
+                                index outside its buffer (the access was
+                                skipped; the state is invalid)                  */
 } osb_status;
 
 /* Arithmetic of the stencil path.  OSB_FP64: everything FP64.  OSB_FP32:

@@ -4,6 +4,12 @@ One translation unit per stencil order plus the misc kernels and the C ABI,
 compiled in parallel, then linked into ``paper_1609_01277_gb300/_lib/libosb.so``.
 ``-Xptxas -v`` output (registers, spills, shared memory) goes to
 ``_lib/ptxas.log``.
+
+``build(bounds_check=True)`` builds the same sources with -DOSB_BOUNDS_CHECK
+into ``_lib_bc/libosb.so``: every index a stage kernel forms is tested against
+its buffer, a failure is recorded in the grid's device error word
+(osb_diagnostics then returns OSB_ERR_BOUNDS) and the access is kept inside
+the buffer.  A test build, slower than the product build.
 """
 from __future__ import annotations
 
@@ -18,6 +24,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libosb.so")
+OUT_BC = os.path.join(HERE, "_lib_bc")
+LIB_BC = os.path.join(OUT_BC, "libosb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "-Xptxas", "-v",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -38,24 +46,26 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "osb.h")]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, jobs: int | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
+def build(force: bool = False, jobs: int | None = None, bounds_check: bool = False) -> str:
+    out, lib = (OUT_BC, LIB_BC) if bounds_check else (OUT, LIB)
+    flags = FLAGS + (["-DOSB_BOUNDS_CHECK"] if bounds_check else [])
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
     srcs = _sources()
-    objs = [os.path.join(OUT, os.path.basename(s)[:-3] + ".o") for s in srcs]
+    objs = [os.path.join(out, os.path.basename(s)[:-3] + ".o") for s in srcs]
 
     def compile_one(pair):
         src, obj = pair
-        r = subprocess.run([cc, *ARCH, *FLAGS, "-c", src, "-o", obj], capture_output=True, text=True)
+        r = subprocess.run([cc, *ARCH, *flags, "-c", src, "-o", obj], capture_output=True, text=True)
         return src, r
 
     logs = []
@@ -64,14 +74,14 @@ def build(force: bool = False, jobs: int | None = None) -> str:
             logs.append(f"== {os.path.basename(src)}\n{r.stdout}{r.stderr}")
             if r.returncode != 0:
                 raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
-    with open(os.path.join(OUT, "ptxas.log"), "w") as f:
+    with open(os.path.join(out, "ptxas.log"), "w") as f:
         f.write("\n".join(logs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

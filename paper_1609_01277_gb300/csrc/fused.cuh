@@ -285,7 +285,7 @@ template <int R>
 __device__ __forceinline__ void wait_plane(Smem<R> &S, const FArgs &a, Ctx &c, int slot) {
     if (c.use_tma) {
         if (!bar_wait(smem_u32(&S.bars[slot]), (c.phase >> slot) & 1u) && threadIdx.x == 0 && a.kerr)
-            atomicExch(a.kerr, 1);
+            atomicOr(a.kerr, KERR_WAIT);
         c.phase ^= 1u << slot;
     } else {
         cp_wait<0>();
@@ -577,6 +577,7 @@ __device__ __forceinline__ void prefetch(const FArgs &a, const Ctx &c, int m, si
 template <int MODE>
 __device__ __forceinline__ void emit(const FArgs &a, const Ctx &c, int m, size_t i, float2 res, float2 srcc,
                                      const Pre<MODE> &pr) {
+    if (!OSB_BC_OK(!c.act0 || i + (c.act1 ? 1 : 0) < (size_t)a.d.n, a.kerr)) return;
     if (a.closure) res = add2(res, gld2(a.closure + (size_t)m * a.d.n + i, c));
     if constexpr (MODE == 1) {
         gst2(a.q_out + m * a.qs + i, fma2(a.adt, res, srcc), c);
@@ -900,6 +901,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const __grid_constant__ FArgs a
             c.eA[t] = ey * G::EW + 2 * ex2;
         }
     }
+    (void)OSB_BC_OK(c.ce >= 0 && c.ce + 1 < G::EP && c.cx >= 0 && c.cx + 1 < G::XS && c.cy >= 0 && c.cy + 1 < G::YS,
+                    a.kerr);
     // phase B halo pairs: the y strips on the first NHY threads (whole warps), then the x strips
     c.chy = c.chx = -1;
     if (tid < G::NHY) {
@@ -945,6 +948,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const __grid_constant__ FArgs a
         c.act0 = xg < d.nx && yg < d.ny;
         c.act1 = xg + 1 < d.nx && yg < d.ny;
         c.gidx = (size_t)yg * d.nx + xg;
+        if (!OSB_BC_OK(!c.act0 || c.gidx + (c.act1 ? 1 : 0) < (size_t)d.nx * d.ny, a.kerr)) c.act0 = c.act1 = false;
+        (void)OSB_BC_OK(c.z0 >= 0 && c.z1 <= d.nz && c.z0 < c.z1 && ((c.x0 - CX) & 3) == 0, a.kerr);
         c.use_tma = tm.use && c.x0 >= CX && c.x0 - CX + G::EW <= d.nx && c.y0 >= 2 * R &&
                     c.y0 - 2 * R + G::EH <= d.ny;
         c.vs = 0;
@@ -952,7 +957,8 @@ __global__ void __launch_bounds__(NT, 2) k_fused(const __grid_constant__ FArgs a
         if (!c.use_tma) {
             for (int e = tid; e < G::EP; e += NT) {
                 const int ey = e / G::EW, ex = e - ey * G::EW;
-                S.off[e] = wrapc(c.y0 + ey - 2 * R, d.ny) * d.nx + wrapc(c.x0 + ex - CX, d.nx);
+                const int v = wrapc(c.y0 + ey - 2 * R, d.ny) * d.nx + wrapc(c.x0 + ex - CX, d.nx);
+                S.off[e] = OSB_BC_OK(v >= 0 && v < d.nx * d.ny, a.kerr) ? v : 0;
             }
         }
         __syncthreads();

@@ -287,7 +287,7 @@ cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const C
 // ---------------------------------------------------------------------------
 template <typename W>
 __global__ void k_halo(W *__restrict__ field, size_t stride, int nz, int H, long long plane, W *__restrict__ lo,
-                       W *__restrict__ hi, int unpack) {
+                       W *__restrict__ hi, int unpack, int *kerr) {
     const long long per = (long long)H * plane;  // words per field and face
     const long long total = 2 * 5 * per;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -298,6 +298,7 @@ __global__ void k_halo(W *__restrict__ field, size_t stride, int nz, int H, long
         const long long j = r - m * per;
         // own planes next to the face (pack) or the ghost planes beyond it (unpack)
         const long long z0 = unpack ? (face ? (long long)(nz - H) : 0) : (face ? (long long)(nz - 2 * H) : (long long)H);
+        if (!OSB_BC_OK(z0 >= 0 && z0 + H <= nz && j < per && m < 5, kerr)) continue;
         W *f = field + m * stride + z0 * plane + j;
         W *b = (face ? hi : lo) + m * per + j;
         if (unpack)
@@ -308,18 +309,18 @@ __global__ void k_halo(W *__restrict__ field, size_t stride, int nz, int H, long
 }
 
 cudaError_t launch_halo(void *field, size_t stride, int esize, int nz, int H, long long plane, void *lo, void *hi,
-                        int unpack, cudaStream_t st) {
+                        int unpack, cudaStream_t st, int *kerr) {
     const long long total = 2LL * 5 * H * plane;
     long long blocks = (total + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
     if (esize == 8)
         k_halo<unsigned long long><<<(int)blocks, 256, 0, st>>>(static_cast<unsigned long long *>(field), stride, nz,
                                                                H, plane, static_cast<unsigned long long *>(lo),
-                                                               static_cast<unsigned long long *>(hi), unpack);
+                                                               static_cast<unsigned long long *>(hi), unpack, kerr);
     else
         k_halo<unsigned int><<<(int)blocks, 256, 0, st>>>(static_cast<unsigned int *>(field), stride, nz, H, plane,
                                                          static_cast<unsigned int *>(lo),
-                                                         static_cast<unsigned int *>(hi), unpack);
+                                                         static_cast<unsigned int *>(hi), unpack, kerr);
     return cudaGetLastError();
 }
 

@@ -436,6 +436,7 @@ const char *osb_status_string(osb_status s) {
         case OSB_ERR_NONFINITE: return "non-finite state";
         case OSB_ERR_TIMEOUT: return "device wait timed out";
         case OSB_ERR_BUFFER: return "buffer too small or misaligned";
+        case OSB_ERR_BOUNDS: return "index outside its buffer (bounds-check build)";
     }
     return "unknown status";
 }
@@ -937,6 +938,8 @@ osb_status osb_diagnostics(osb_grid *g, osb_diag *out) {
     for (int m = 0; m < 5; ++m) out->total[m] = h[2 + m];
     out->nonfinite = (long long)h[7];
     out->max_cfl = h[8];
+    if (herr & KERR_BOUNDS)
+        return fail(OSB_ERR_BOUNDS, "bounds-check build: a kernel computed an index outside its buffer; the state is invalid");
     if (herr) return fail(OSB_ERR_TIMEOUT, "a bounded in-kernel wait of an earlier step ran out; the state is invalid");
     if (out->nonfinite > 0) return fail(OSB_ERR_NONFINITE, "state holds non-finite values");
     return OSB_OK;
@@ -1366,7 +1369,7 @@ static osb_status halo_common(osb_grid *g, int source, void *lo, void *hi, int u
     int esize = 0;
     halo_source(g, source, &f, &stride, &esize);
     const cudaError_t e = launch_halo(f, stride, esize, g->d.nz, g->slab_h, (long long)g->d.nx * g->d.ny, lo, hi,
-                                      unpack, g->st);
+                                      unpack, g->st, g->kerr);
     if (e != cudaSuccess) return cuda_fail(e, unpack ? "halo unpack" : "halo pack");
     return OSB_OK;
 }

@@ -18,6 +18,23 @@
 
 namespace osb {
 
+// Device error word of a grid (StageArgs::kerr): bit 0 a bounded in-kernel
+// wait ran out, bit 1 (bounds-check build, -DOSB_BOUNDS_CHECK) an index
+// computed by a stage kernel fell outside its buffer.  The bounds-check build
+// tests each index where it is formed (neighbour offsets, tile and ring
+// indices, global point indices, halo planes), records a failure here and
+// replaces the index by 0, so the access stays inside the buffer: no trap.
+constexpr int KERR_WAIT = 1, KERR_BOUNDS = 2;
+#ifdef OSB_BOUNDS_CHECK
+__device__ __forceinline__ bool bc_fail(int *kerr) {
+    if (kerr) atomicOr(kerr, KERR_BOUNDS);
+    return true;
+}
+#define OSB_BC_OK(cond, kerr) ((cond) || !::osb::bc_fail(kerr))
+#else
+#define OSB_BC_OK(cond, kerr) true
+#endif
+
 constexpr int MAXR = 6;  // orders 2..12
 constexpr int BX = 32, BY = 8;  // thread block / tile of the per-point stage kernels
 
@@ -238,7 +255,7 @@ cudaError_t launch_diagnostics(const Dims &d, const Phys &ph, int order, const C
 // planes, H ghost planes at each end) into lo/hi, or unpack lo/hi into the
 // ghost planes; 5 fields of esize-byte words (4 or 8), field stride in words.
 cudaError_t launch_halo(void *field, size_t stride, int esize, int nz, int H, long long plane, void *lo, void *hi,
-                        int unpack, cudaStream_t st);
+                        int unpack, cudaStream_t st, int *kerr);
 int diag_num_partials(const Dims &d);
 cudaError_t launch_to_dd(const double *U, size_t u_stride, dd *q, size_t q_stride, int n, double e_ref,
                          cudaStream_t st);

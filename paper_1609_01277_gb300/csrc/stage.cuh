@@ -110,7 +110,7 @@ struct Nbr : NbrMask<SYM> {
     int x[2 * R + 1];  // x + k
     int y[2 * R + 1];  // (y + k) * nx
     int z[2 * R + 1];  // (z + k) * nx * ny
-    __device__ __forceinline__ void init(int px, int py, int pz, const Dims &d) {
+    __device__ __forceinline__ void init(int px, int py, int pz, const Dims &d, int *kerr = nullptr) {
 #pragma unroll
         for (int k = -R; k <= R; ++k) {
             if constexpr (SYM) {
@@ -127,7 +127,26 @@ struct Nbr : NbrMask<SYM> {
                 z[k + R] = wrapc(pz + k, d.nz) * d.nx * d.ny;
             }
         }
+#ifdef OSB_BOUNDS_CHECK
+        check(px, py, pz, d, kerr);
+#else
+        (void)kerr;
+#endif
     }
+#ifdef OSB_BOUNDS_CHECK
+    // every neighbour inside the field: x in [0, nx), y a row start, z a plane start
+    __device__ __forceinline__ void check(int px, int py, int pz, const Dims &d, int *kerr) {
+        bool ok = px >= 0 && px < d.nx && py >= 0 && py < d.ny && pz >= 0 && pz < d.nz;
+        const int plane = d.nx * d.ny;
+#pragma unroll
+        for (int k = 0; k < 2 * R + 1; ++k)
+            ok = ok && x[k] >= 0 && x[k] < d.nx && y[k] >= 0 && y[k] < plane && y[k] % d.nx == 0 && z[k] >= 0 &&
+                 z[k] < d.n && z[k] % plane == 0;
+        if (!OSB_BC_OK(ok, kerr))
+#pragma unroll
+            for (int k = 0; k < 2 * R + 1; ++k) x[k] = y[k] = z[k] = 0;
+    }
+#endif
     template <int AX>
     __device__ __forceinline__ int at(int k) const {
         if (AX == 0) return z[R] + y[R] + x[R + k];
@@ -356,7 +375,8 @@ __device__ __forceinline__ void block_record2(double a, double b, double *rec) {
 // ---------------------------------------------------------------------------
 template <int POL, typename S, typename T>
 __device__ __forceinline__ void prim_point(const StageArgs &a, int x, int y, int z) {
-    const int i = (z * a.d.ny + y) * a.d.nx + x;
+    int i = (z * a.d.ny + y) * a.d.nx + x;
+    if (!OSB_BC_OK(x >= 0 && x < a.d.nx && y >= 0 && y < a.d.ny && z >= 0 && z < a.d.nz, a.kerr)) i = 0;
     const S *Q = static_cast<const S *>(a.src);
     const size_t qs = a.src_stride;
     T *aux = static_cast<T *>(a.aux);
@@ -417,7 +437,7 @@ __device__ __forceinline__ void point_diag_dd(double *dg, const dd &rho, const d
 template <int POL, typename S, int R, bool SYM>
 __device__ __forceinline__ void grad_point_dd_b(const StageArgs &a, int x, int y, int z, double *dg) {
     Nbr<R, SYM> nb;
-    nb.init(x, y, z, a.d);
+    nb.init(x, y, z, a.d, a.kerr);
     const int i = nb.center();
     const Coef<dd> &c = a.cdd;
     dd *aux = static_cast<dd *>(a.aux);
@@ -459,7 +479,7 @@ __device__ __forceinline__ void grad_point(const StageArgs &a, int x, int y, int
         return;
     } else {
     Nbr<R, SYM> nb;
-    nb.init(x, y, z, a.d);
+    nb.init(x, y, z, a.d, a.kerr);
     const int i = nb.center();
     const FoldW<T> &fw = FoldPick<T>::get(a);
     T *aux = static_cast<T *>(a.aux);
@@ -523,7 +543,7 @@ __device__ __forceinline__ void acc_add(dd_acc &acc, const dd &w, const dd &x) {
 template <int POL, typename S, int R, bool SYM>
 __device__ __forceinline__ void grad_point_dd(const StageArgs &a, int x, int y, int z, double *dg) {
     Nbr<R, SYM> nb;
-    nb.init(x, y, z, a.d);
+    nb.init(x, y, z, a.d, a.kerr);
     const int i = nb.center();
     const Coef<dd> &c = a.cdd;
     dd *aux = static_cast<dd *>(a.aux);
@@ -762,7 +782,7 @@ __device__ __forceinline__ void adv_axis(T (&res)[5], const S *Q, size_t qs, con
 template <int POL, typename S, typename T, int R, int MODE, bool VB, bool SYM = false>
 __device__ __forceinline__ void resid_point(const StageArgs &a, int x, int y, int z) {
     Nbr<R, SYM> nb;
-    nb.init(x, y, z, a.d);
+    nb.init(x, y, z, a.d, a.kerr);
     const int i = nb.center();
     const Coef<T> &c = CoefPick<T>::get(a);
     const S *Q = static_cast<const S *>(a.src);

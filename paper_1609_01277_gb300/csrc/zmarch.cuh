@@ -242,7 +242,7 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
     auto wait_plane = [&](int L) {
         if (use_tma) {
             const int s = ((L % G::NS) + G::NS) % G::NS;
-            if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
+            if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicOr(a.kerr, KERR_WAIT);
             phase ^= 1u << s;
         } else {
             cp_wait<G::PF - 1>();
@@ -308,7 +308,8 @@ __device__ __forceinline__ void zflux_body(const StageArgs &a, const ZTma &tm, i
             dg_ens += double(0.5f * rho * fmaf(o0, o0, fmaf(o1, o1, o2 * o2)));
         }
         if (active) {
-            const size_t i = (size_t)zo * plane + coff;
+            size_t i = (size_t)zo * plane + coff;
+            if (!OSB_BC_OK(zo >= 0 && zo < d.nz && coff >= 0 && coff < plane, a.kerr)) i = 0;
             aux[A_FX * as + i] = hE * u - (u * txx + v * txy + w * txz);
             aux[A_FY * as + i] = hE * v - (u * txy + v * tyy + w * tyz);
             aux[A_FZ * as + i] = hE * w - (u * txz + v * tyz + w * tzz);
@@ -424,7 +425,7 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
     auto wait_plane = [&](int L) {
         if (use_tma) {
             const int s = ((L % G::NS) + G::NS) % G::NS;
-            if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicExch(a.kerr, 1);
+            if (!bar_wait(smem_u32(&bars[s]), (phase >> s) & 1u) && tid == 0 && a.kerr) atomicOr(a.kerr, KERR_WAIT);
             phase ^= 1u << s;
         } else {
             cp_wait<G::PF - 1>();
@@ -480,7 +481,8 @@ __device__ __forceinline__ void zrhs_body(const StageArgs &a, const ZTma &tm, in
         const int zo = L - R;
         if (zo < z0) continue;
         const int so = ((zo % G::NS) + G::NS) % G::NS;
-        const size_t i = (size_t)zo * plane + coff;
+        size_t i = (size_t)zo * plane + coff;
+        if (!OSB_BC_OK(!active || (zo >= 0 && zo < d.nz && coff >= 0 && coff < plane), a.kerr)) i = 0;
         // FP64 accumulator of this point: issue the loads before the plane work
         double Ui[5];
         float divc;

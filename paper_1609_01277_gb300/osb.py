@@ -22,7 +22,7 @@ OSB_FP64, OSB_FP32, OSB_DF64 = 0, 1, 2
 OSB_VISC_A, OSB_VISC_B = 0, 1
 OSB_BC_PERIODIC, OSB_BC_SYMMETRIC = 0, 1
 STATUS = {0: "OSB_OK", 1: "OSB_ERR_INVALID_ARG", 2: "OSB_ERR_UNSUPPORTED", 3: "OSB_ERR_CUDA",
-          4: "OSB_ERR_NONFINITE", 5: "OSB_ERR_TIMEOUT", 6: "OSB_ERR_BUFFER"}
+          4: "OSB_ERR_NONFINITE", 5: "OSB_ERR_TIMEOUT", 6: "OSB_ERR_BUFFER", 7: "OSB_ERR_BOUNDS"}
 
 # every entry point declared in include/osb.h
 EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_grid_destroy",

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(osb):
 
 def test_status_strings(osb):
     L = osb.load()
-    for code in range(7):
+    for code in range(8):
         assert L.osb_status_string(code)
     assert L.osb_status_string(0) == b"ok"
 
