@@ -2,10 +2,14 @@
 ABI: forward, loss and parameter gradients, Adam, box filter, the correction
 added to R, and what training gains over the solver without it.
 
-Tolerances: BF16 operands (unit roundoff 2^-9) with FP32 accumulation on the
-GPU vs float64 sums on the CPU; an element whose pre-activation sits at a BF16
-rounding boundary can round differently, so outputs and gradients are held
-to a relative L2 of 1e-2 (loss 1e-3)."""
+Tolerances: the oracle rounds operands and activations to BF16 where the
+kernels do, so what remains is FP32 accumulation on the GPU against float64
+sums on the CPU, and the rare element whose pre-activation sits at a BF16
+rounding boundary and rounds the other way.  Measured on 8 to 32 points per
+axis: forward <= 6.5e-4, parameter gradients <= 3.8e-4, loss <= 2.7e-5
+(relative L2); held to 3e-3, 3e-3 and 2e-4.  Grids whose y extent is a
+multiple of 16 run the tcgen05 convolutions, the others the mma.sync tiles:
+both are covered."""
 from __future__ import annotations
 
 import numpy as np
@@ -49,12 +53,17 @@ def _rel(a, b):
     return float(np.linalg.norm(np.ravel(a - b)) / np.linalg.norm(np.ravel(b)))
 
 
-def test_forward_matches_oracle(mods):
+FWD_TOL, GRAD_TOL, LOSS_TOL = 3e-3, 3e-3, 2e-4
+SHAPES = [(16, 8, 8), (16, 16, 8), (24, 32, 8)]   # mma.sync tiles; tcgen05 (y multiple of 16)
+
+
+@pytest.mark.parametrize("n", SHAPES)
+def test_forward_matches_oracle(mods, n):
     osb, closure, torch = mods
-    c, theta, Q, _, mean, std, out = _setup(mods)
+    c, theta, Q, _, mean, std, out = _setup(mods, n=n)
     Cg = c.forward(torch.from_numpy(Q).cuda()).cpu().numpy()
     Co = co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16")
-    assert _rel(Cg, Co) < 1e-2
+    assert _rel(Cg, Co) < FWD_TOL
 
 
 def test_dissipative_forward_matches_oracle(mods):
@@ -66,22 +75,23 @@ def test_dissipative_forward_matches_oracle(mods):
     finally:
         c.set_dissipative(False)
     Co = co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16", dissipative=True)
-    assert _rel(Cg, Co) < 1e-2
+    assert _rel(Cg, Co) < FWD_TOL
     u = Q[1:4] / Q[0]
     dg = np.sum(u * Cg[1:4].astype(np.float64), axis=0)
     assert np.all(dg <= 1e-5 * np.sum(np.abs(u * Cg[1:4]), axis=0) + 1e-30)
 
 
-def test_loss_and_gradients_match_oracle(mods):
+@pytest.mark.parametrize("n", [(16, 8, 12), (16, 16, 8), (32, 16, 12)])
+def test_loss_and_gradients_match_oracle(mods, n):
     osb, closure, torch = mods
-    c, theta, Q, C, mean, std, out = _setup(mods, n=(16, 8, 12), seed=3)
+    c, theta, Q, C, mean, std, out = _setup(mods, n=n, seed=3)
     loss, grad = c.loss_grad(torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda())
     lo, go = co.loss_grad(theta.astype(np.float64), Q, C, mean, std, out, mode="bf16")
-    assert float(loss.item()) == pytest.approx(lo, rel=1e-3)
+    assert float(loss.item()) == pytest.approx(lo, rel=LOSS_TOL)
     g = grad.cpu().numpy().astype(np.float64)
     P, Po = co.unpack(g), co.unpack(go)
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
-        assert _rel(P[name], Po[name]) < 2e-2, name
+        assert _rel(P[name], Po[name]) < GRAD_TOL, name
 
 
 def test_loss_weight_scales_loss_and_gradient(mods):
@@ -167,13 +177,13 @@ def test_tensor_core_convolutions_match_oracle(mods):
     c, theta, Q, C, mean, std, out = _setup(mods, n=(16, 16, 8), seed=11)
     Qd, Cd = torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda()
     Cg = c.forward(Qd).cpu().numpy()
-    assert _rel(Cg, co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16")) < 1e-2
+    assert _rel(Cg, co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16")) < FWD_TOL
     loss, grad = c.loss_grad(Qd, Cd)
     lo, go = co.loss_grad(theta.astype(np.float64), Q, C, mean, std, out, mode="bf16")
-    assert float(loss.item()) == pytest.approx(lo, rel=1e-3)
+    assert float(loss.item()) == pytest.approx(lo, rel=LOSS_TOL)
     P, Po = co.unpack(grad.cpu().numpy().astype(np.float64)), co.unpack(go)
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
-        assert _rel(P[name], Po[name]) < 2e-2, name
+        assert _rel(P[name], Po[name]) < GRAD_TOL, name
     c.status()
 
 
