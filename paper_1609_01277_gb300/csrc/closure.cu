@@ -326,6 +326,278 @@ __global__ void __launch_bounds__(128) k_conv_tc(int nx, int ny, int nz, const u
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(taddr));
 }
 
+// ---------------------------------------------------------------------------
+// The tcgen05 convolution as a z-march: one CTA owns a column of 8 x 16 bricks
+// and a chunk of z planes.  The weights stay in shared memory for the whole
+// chunk; input planes (the 10 x 18 haloed tile of one z, CI channels) stream
+// through a ring of TC_SLOTS slots two planes ahead of use (cp.async, wrapped
+// periodically); two TMEM accumulators alternate between planes, so one
+// thread of a fifth warp issues the 27 * CI/16 MMAs of output plane z while
+// warps 0-3 read the accumulator of plane z-1 and write it out (a thread that
+// queues many MMAs can stall at issue: kept apart, that stall does not hold
+// back an epilogue).  Per output plane:
+//   (a) every thread waits for its copies of plane z+1, fences them to the
+//       async proxy, block barrier (which also means the epilogue of plane z-2
+//       has read accumulator z&1);
+//   (b) warp 4 issues plane z's MMAs (taps dz = -1, 0, +1 read the slots of
+//       planes z-1, z, z+1) and commits them to mbarrier z&1, then goes on to
+//       the next barrier;
+//   (c) warps 0-3 wait for plane z-1's commit (bounded), which also frees the
+//       slot of plane z-2 (its last reader was plane z-1's MMAs);
+//   (d) copies of plane z+3 go into that slot;
+//   (e) epilogue of plane z-1.
+// Shared memory at CI = 32: weights 55.3 KB + ring 5 x 11.5 KB: two CTAs per SM.
+// The output layer (CO = 8, FP32 out) runs as N = 16 MMAs against weights
+// padded with zero rows.
+// ---------------------------------------------------------------------------
+constexpr int TC_SLOTS = 5;
+constexpr int TC_THREADS = 160;  // warps 0-3: copies and epilogue (one TMEM lane quarter each); warp 4: MMA issue
+constexpr int TPP = THX * THY;  // 180 haloed positions of one plane
+
+// z planes per CTA: the chunk count c minimising (CTA rounds of two per SM)
+// x (planes per CTA + 3 for the ring start); OSB_TC_ZCHUNK overrides.
+inline int tc_zchunk(int cols, int nz) {
+    if (const char *e = getenv("OSB_TC_ZCHUNK")) {
+        const int v = atoi(e);
+        if (v > 0) return v < nz ? v : nz;
+    }
+    constexpr long long slots = 2 * 152;
+    long long best = -1;
+    int bz = nz;
+    for (int c = 1; c <= nz; ++c) {
+        const int zc = (nz + c - 1) / c;
+        const int cc = (nz + zc - 1) / zc;
+        const long long rounds = ((long long)cols * cc + slots - 1) / slots;
+        const long long cost = rounds * (zc + 3);
+        if (best < 0 || cost < best) best = cost, bz = zc;
+    }
+    return bz;
+}
+
+// MMA width N for CO output channels: M = 128 takes N in multiples of 16
+template <int CO>
+__host__ __device__ constexpr int tc_n() {
+    return CO < 16 ? 16 : CO;
+}
+
+template <int CI, int CO>
+constexpr size_t tcp_smem() {
+    return (size_t)27 * CI * tc_n<CO>() * 2 + (size_t)TC_SLOTS * TPP * CI * 2;
+}
+
+// TMEM -> registers: this warp's 32 lanes (points), NC consecutive columns
+template <int NC>
+__device__ __forceinline__ void tm_ld(uint32_t taddr, uint32_t (&r)[NC]) {
+    static_assert(NC == 8 || NC == 32, "8 or 32 columns");
+    if constexpr (NC == 32) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+              "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+              "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+    } else {
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                     : "r"(taddr));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, bool accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"((uint32_t)accumulate));
+}
+
+__device__ __forceinline__ bool tc_bar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (unsigned it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (!done && it > 16) __nanosleep(32);
+    }
+    return done != 0;
+}
+
+template <int CI, int CO, int EPI>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tcp(int nx, int ny, int nz, int zchunk, const uint16_t *__restrict__ in,
+                                                  const uint16_t *__restrict__ W, const float *__restrict__ bias,
+                                                  const uint16_t *__restrict__ mask, void *__restrict__ out,
+                                                  int *__restrict__ err) {
+    static_assert((CO == 32 && EPI != EPI_LIN) || (CO == 8 && EPI == EPI_LIN), "hidden or output layer");
+    constexpr int NCH = CI / 8;
+    constexpr int NT = tc_n<CO>();          // MMA N and TMEM columns per accumulator
+    constexpr uint32_t TCOLS = 2 * NT < 32 ? 32 : 2 * NT;  // allocation: a power of two >= 32
+    constexpr uint32_t SLOT = (uint32_t)TPP * CI * 2;  // bytes of one ring slot: [NCH][180][8 ch]
+    extern __shared__ __align__(128) uint8_t tsm[];
+    uint8_t *Bw = tsm;                          // weights [27][NCH][NT][8 ch], rows >= CO zero
+    uint8_t *A = tsm + (size_t)27 * CI * NT * 2;  // ring
+    __shared__ uint32_t taddr_s;
+    __shared__ __align__(8) uint64_t bars[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bx = nx / TBX, by = ny / TBY;
+    const int colx = blockIdx.x % (bx * by), chunk = blockIdx.x / (bx * by);
+    const int x0 = (colx % bx) * TBX, y0 = (colx / bx) * TBY;
+    const int z0 = chunk * zchunk, z1 = min(z0 + zchunk, nz);
+
+    if (warp == 0) {
+        const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&taddr_s);
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa), "n"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    const uint32_t bar0 = (uint32_t)__cvta_generic_to_shared(&bars[0]);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // weights [27][CO][CI] -> [27][NCH][NT][8], with the first plane's copies
+    for (int e = tid; e < 27 * NT * NCH && warp < 4; e += 128) {
+        const int k = e / (NT * NCH), n = (e / NCH) % NT, ch = e % NCH;
+        uint8_t *dst = Bw + (((size_t)k * NCH + ch) * NT + n) * 16;
+        if (n < CO)
+            tc_cp_async16(dst, W + ((size_t)k * CO + n) * CI + ch * 8);
+        else
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // input plane zp (any integer, wrapped) -> its ring slot; one commit group per plane
+    auto load_plane = [&](int zp) {
+        const int slot = ((zp - z0 + 1) % TC_SLOTS + TC_SLOTS) % TC_SLOTS;  // plane z0-1 in slot 0
+        const int gz = wrapi(wrapi(zp, nz), nz);
+        uint8_t *As = A + (size_t)slot * SLOT;
+        for (int e = tid; e < TPP * NCH && warp < 4; e += 128) {
+            const int pos = e / NCH, ch = e - pos * NCH;
+            const int hx = pos % THX, hy = pos / THX;
+            const int gx = wrapi(x0 + hx - 1, nx), gy = wrapi(y0 + hy - 1, ny);
+            const size_t gp = ((size_t)gz * ny + gy) * nx + gx;
+            tc_cp_async16(As + ((size_t)ch * TPP + pos) * 16, in + gp * CI + ch * 8);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    load_plane(z0 - 1);
+    load_plane(z0);
+    load_plane(z0 + 1);
+    load_plane(z0 + 2);
+    __syncthreads();  // TMEM address and barrier initialisation visible
+    const uint32_t taddr = taddr_s;
+    const uint32_t a0 = (uint32_t)__cvta_generic_to_shared(A), b0 = (uint32_t)__cvta_generic_to_shared(Bw);
+    constexpr uint32_t idesc = tc_idesc<NT>();
+    const uint64_t adesc0 = tc_desc(a0, TPP * 16, THX * 16), bdesc0 = tc_desc(b0, NT * 16, 128);
+    const int p = warp * 32 + lane, px = p % TBX, py = p / TBX;  // this thread's row of the brick
+
+    auto epilogue = [&](int j) {  // output plane z0 + j from accumulator j & 1
+        uint32_t r[CO];
+        tm_ld<CO>(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(j & 1) * NT, r);
+        const size_t gp = ((size_t)(z0 + j) * ny + (y0 + py)) * nx + (x0 + px);
+        float v[CO];
+#pragma unroll
+        for (int c = 0; c < CO; ++c) v[c] = __uint_as_float(r[c]);
+        if (EPI != EPI_MASK) {
+#pragma unroll
+            for (int c = 0; c < CO; ++c) v[c] += bias[c];
+        }
+        if (EPI == EPI_RELU) {
+#pragma unroll
+            for (int c = 0; c < CO; ++c) v[c] = fmaxf(v[c], 0.f);
+        }
+        if (EPI == EPI_MASK) {
+            const uint4 *mk = reinterpret_cast<const uint4 *>(mask + gp * CO);
+#pragma unroll
+            for (int q = 0; q < CO / 8; ++q) {
+                const uint4 m4 = mk[q];
+                const uint32_t mw[4] = {m4.x, m4.y, m4.z, m4.w};
+#pragma unroll
+                for (int h = 0; h < 8; ++h) {
+                    const uint16_t mb = (uint16_t)(mw[h / 2] >> (16 * (h & 1)));
+                    if (!(bf16_val(mb) > 0.f)) v[q * 8 + h] = 0.f;
+                }
+            }
+        }
+        if (EPI == EPI_LIN) {  // FP32 out
+            float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(out) + gp * CO);
+#pragma unroll
+            for (int q = 0; q < CO / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {  // BF16 out
+            uint4 *o = reinterpret_cast<uint4 *>(static_cast<uint16_t *>(out) + gp * CO);
+#pragma unroll
+            for (int q = 0; q < CO / 8; ++q) {
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h)
+                    w[h] = (uint32_t)bf16_bits(v[q * 8 + 2 * h]) | ((uint32_t)bf16_bits(v[q * 8 + 2 * h + 1]) << 16);
+                o[q] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    };
+
+    bool ok = true;
+#pragma unroll 1
+    for (int j = 0; j < z1 - z0; ++j) {
+        // (a) planes up to z+1 in shared memory, visible to the tensor cores
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // (b) plane z's MMAs into accumulator j & 1.  Descriptors are the base
+        // descriptors plus constant offsets (the 14-bit address field holds
+        // the whole shared window, so the sums never carry out of it).
+        if (tid == 128) {
+            const uint32_t acc_addr = taddr + (uint32_t)(j & 1) * NT;
+            uint64_t adz[3];
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)  // plane z - 1 + dz lives in slot (j + dz) % TC_SLOTS
+                adz[dz] = adesc0 + (uint64_t)((((j + dz) % TC_SLOTS) * SLOT) >> 4);
+#pragma unroll
+            for (int k = 0; k < 27; ++k) {
+                const int dx = k % 3, dy = (k / 3) % 3, dz = k / 9;
+#pragma unroll
+                for (int s = 0; s < CI / 16; ++s) {
+                    const uint64_t ad = adz[dz] + (uint64_t)((((2 * s) * TPP + dy * THX + dx) * 16) >> 4);
+                    const uint64_t bd = bdesc0 + (uint64_t)((((k * NCH + 2 * s) * NT) * 16) >> 4);
+                    tc_mma(acc_addr, ad, bd, idesc, (k | s) != 0);
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar0 + 8u * (uint32_t)(j & 1))
+                         : "memory");
+        }
+        if (warp == 4) continue;  // the MMA warp: on to the next plane's barrier
+        // (c) plane z-1's MMAs done: its accumulator is ready, the slot of plane z-2 free
+        if (j >= 1) {
+            if (!tc_bar_wait(bar0 + 8u * (uint32_t)((j - 1) & 1), (uint32_t)(((j - 1) >> 1) & 1))) ok = false;
+            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        }
+        // (d) plane z+3 into the slot of plane z-2
+        if (z0 + j + 3 <= z1)
+            load_plane(z0 + j + 3);
+        else
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+        // (e) epilogue of plane z-1
+        if (j >= 1 && ok) epilogue(j - 1);
+    }
+    const int last = z1 - z0 - 1;
+    if (last >= 0 && warp < 4) {
+        if (!tc_bar_wait(bar0 + 8u * (uint32_t)(last & 1), (uint32_t)((last >> 1) & 1))) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) epilogue(last);
+    }
+    if (!ok && lane == 0) atomicExch(err, 1);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "n"(TCOLS));
+}
+
 template <int CI, int CO>
 constexpr size_t conv_smem() {
     return (size_t)(NH * (CI + 8) + 27 * CO * (CI + 8)) * sizeof(uint16_t);
@@ -654,23 +926,39 @@ size_t carve(char *base, int n, Buffers *B) {
 }
 
 
-int g_tc_mode = -1;  // 1: tensor-core (tcgen05) convolutions where applicable, 0: mma.sync only
+// 1: tensor-core (tcgen05) z-marching convolutions where applicable; 2: the
+// same MMAs one brick per CTA (k_conv_tc); 0: mma.sync only.  OSB_CLOSURE_MMA
+// = "sync" | "brick" selects the others.
+int g_tc_mode = -1;
 
 template <int CI, int CO, int EPI>
 cudaError_t conv(int nx, int ny, int nz, const uint16_t *in, const uint16_t *W, const float *bias, const uint16_t *mask,
                  void *out, int *tcerr, cudaStream_t st) {
     {
         const char *env = getenv("OSB_CLOSURE_MMA");
-        g_tc_mode = !(env && strcmp(env, "sync") == 0);
+        g_tc_mode = !env ? 1 : strcmp(env, "sync") == 0 ? 0 : strcmp(env, "brick") == 0 ? 2 : 1;
     }
-    if constexpr (CO == 32 && EPI != EPI_LIN) {
-        if (g_tc_mode && ny % TBY == 0 && nx % TBX == 0 && tcerr) {
-            constexpr size_t sm = tc_smem_used<CI, CO>();
-            cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if constexpr ((CO == 32 && EPI != EPI_LIN) || (CO == 8 && EPI == EPI_LIN)) {
+        if constexpr (CO == 32) {
+            if (g_tc_mode == 2 && ny % TBY == 0 && nx % TBX == 0 && tcerr) {
+                constexpr size_t sm = tc_smem_used<CI, CO>();
+                cudaError_t e = cudaFuncSetAttribute(k_conv_tc<CI, CO, EPI>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (e != cudaSuccess) return e;
+                const int bricks = (nx / TBX) * (ny / TBY) * nz;
+                k_conv_tc<CI, CO, EPI><<<bricks, 128, sm, st>>>(nx, ny, nz, in, W, bias, mask, out, tcerr);
+                return cudaGetLastError();
+            }
+        }
+        if (g_tc_mode == 1 && ny % TBY == 0 && nx % TBX == 0 && tcerr) {
+            constexpr size_t sm = tcp_smem<CI, CO>();
+            cudaError_t e = cudaFuncSetAttribute(k_conv_tcp<CI, CO, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)sm);
             if (e != cudaSuccess) return e;
-            const int bricks = (nx / TBX) * (ny / TBY) * nz;
-            k_conv_tc<CI, CO, EPI><<<bricks, 128, sm, st>>>(nx, ny, nz, in, W, bias, mask, out, tcerr);
+            const int cols = (nx / TBX) * (ny / TBY);
+            const int zc = tc_zchunk(cols, nz);
+            const int ctas = cols * ((nz + zc - 1) / zc);
+            k_conv_tcp<CI, CO, EPI><<<ctas, TC_THREADS, sm, st>>>(nx, ny, nz, zc, in, W, bias, mask, out, tcerr);
             return cudaGetLastError();
         }
     }

@@ -197,3 +197,40 @@ def test_tensor_core_and_mma_sync_paths_agree(mods, monkeypatch):
     tc = c.forward(Qd).cpu().numpy()
     c.status()
     assert _rel(tc, ref) < 5e-3
+
+
+@pytest.mark.parametrize("zchunk", ["1", "3", "5"])
+def test_z_marching_tensor_core_chunks(mods, monkeypatch, zchunk):
+    """The z-marching tcgen05 convolutions over z chunks of 1, 3 (ragged last
+    chunk of 2) and 5 (3) planes agree bit for bit with one chunk of all 8
+    planes (the same MMAs per accumulator), and with the CPU oracle."""
+    osb, closure, torch = mods
+    c, theta, Q, C, mean, std, out = _setup(mods, n=(16, 32, 8), seed=17)
+    Qd, Cd = torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda()
+    monkeypatch.setenv("OSB_CLOSURE_MMA", "tc")
+    monkeypatch.setenv("OSB_TC_ZCHUNK", "8")
+    ref = c.forward(Qd).cpu().numpy()
+    lr, gr = c.loss_grad(Qd, Cd)
+    lr, gr = float(lr.item()), gr.cpu().numpy()
+    monkeypatch.setenv("OSB_TC_ZCHUNK", zchunk)
+    got = c.forward(Qd).cpu().numpy()
+    lt, gt = c.loss_grad(Qd, Cd)
+    c.status()
+    assert np.array_equal(got, ref)
+    assert float(lt.item()) == pytest.approx(lr, rel=1e-6)
+    assert _rel(gt.cpu().numpy(), gr) < 1e-6
+    assert _rel(got, co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16")) < FWD_TOL
+
+
+def test_brick_and_z_marching_tensor_core_kernels_agree(mods, monkeypatch):
+    """One brick per CTA (hidden layers on tcgen05, output layer on mma.sync)
+    against the z-marching kernels (all three layers on tcgen05)."""
+    osb, closure, torch = mods
+    c, theta, Q, C, *_ = _setup(mods, n=(16, 32, 8), seed=19)
+    Qd = torch.from_numpy(Q).cuda()
+    monkeypatch.setenv("OSB_CLOSURE_MMA", "brick")
+    ref = c.forward(Qd).cpu().numpy()
+    monkeypatch.setenv("OSB_CLOSURE_MMA", "tc")
+    got = c.forward(Qd).cpu().numpy()
+    c.status()
+    assert _rel(got, ref) < 1e-5
