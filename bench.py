@@ -117,6 +117,9 @@ def peaks():
         p["hbm_gbs"] = m.get("hbm_gbs")
         p["src"] = "measured"
         p["sm_max_mhz"] = m.get("sm_max_mhz")
+        p["bf16_tflops"] = m.get("bf16_tflops")
+    if p.get("bf16_tflops") is None:
+        p["bf16_tflops"] = 1900.0  # fallback burst figure
     if p["hbm_gbs"] is None:
         p["hbm_gbs"] = 6800.0
         p["src"] = "fallback"
@@ -598,6 +601,14 @@ def run_ours(args):
             "closure_cost_vs_plain_32": best["seconds"] / r["plain"]["seconds"],
             "speedup_vs_filtered_fine_run": r["seconds"]["fine_data"] / best["seconds"],
             "fallback_t": best["fallback_t"]}
+        # the network's kernels on their own: forward and loss + gradient at 128^3
+        from paper_1609_01277_gb300 import experiments as ex
+        kt = ex.closure_timing(128, reps=10)
+        keep["summary"].update({
+            "forward_ms_128": kt["forward_ms"], "loss_grad_ms_128": kt["loss_grad_ms"],
+            "forward_tflops_128": kt["forward_tflops"],
+            "forward_bf16_frac": kt["forward_tflops"] / pk["bf16_tflops"],
+            "forward_flops": "2 x 27 x (5*32 + 32*32 + 32*5) per point (the network's, unpadded)"})
         variants["closure_tgv128to32"] = keep
 
     cpu = None
