@@ -310,9 +310,10 @@ def run_ensemble(torch, osb, inputs, steps, precision):
         g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
         grids.append(g)
     tuned = {}
-    for g in grids:
-        if g.cfg.nx not in tuned:
-            tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
+    if ensemble_launches(precision, len(specs))["mode"] == "persistent":  # tile depths of the persistent kernel
+        for g in grids:
+            if g.cfg.nx not in tuned:
+                tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
     pts = sum(g.cfg.n for g in grids)
     osb.batch_step(grids, steps)          # warm-up + graph capture
     torch.cuda.synchronize()
@@ -334,8 +335,26 @@ def run_ensemble(torch, osb, inputs, steps, precision):
     return {"instances": len(specs), "points": pts, "steps": steps, "tile_depth": tuned,
             "value": steps * 3 * pts / t_batch, "ms_per_step": 1e3 * t_batch / steps,
             "per_grid_launch_value": steps * 3 * pts / t_seq, "speedup_vs_per_grid_launches": t_seq / t_batch,
-            "ke_first4": ke, "launches_per_step": 1,
-            "per_grid_launches_per_step": (6 if precision == "fp32" else 9) * len(specs),
+            "ke_first4": ke, **ensemble_launches(precision, len(specs))}
+
+
+def ensemble_launches(precision, count):
+    """How the library runs an ensemble step (OSB_BATCH_MODE overrides the
+    default): FP64 and FP32 in one persistent launch for all steps;
+    double-float as each grid's own step graph (9 kernels) replayed on 8
+    concurrent library streams, the grids spread over them by points."""
+    mode = os.environ.get("OSB_BATCH_MODE") or ("streams" if precision == "df64" else "persistent")
+    if mode == "phases" and precision != "df64":
+        mode = "persistent"
+    per_grid = (3 if precision == "fp32" else 9) * count
+    if mode == "streams":
+        return {"mode": "streams", "launches_per_step": f"{count} step graphs ({per_grid} kernels) on 8 streams",
+                "per_grid_launches_per_step": per_grid, "items": "per-grid step graphs"}
+    if mode == "phases":
+        return {"mode": "phases", "launches_per_step": 9, "per_grid_launches_per_step": per_grid,
+                "items": "per-phase launches of three-kernel point items"}
+    return {"mode": "persistent", "launches_per_step": "1 persistent launch for all steps",
+            "per_grid_launches_per_step": (6 if precision == "fp32" else 9) * count,
             "items": "z-march column items" if precision == "fp32" else "three-kernel point items"}
 
 

@@ -210,29 +210,42 @@ osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
 
 /* Advances n independent grids (an ensemble of uneven sizes, Reynolds and
  * Mach numbers and time steps; an extension of the paper's Section
- * 3.3 solver) by nsteps RK3 steps each, in ONE persistent kernel launch that
- * is captured into a CUDA graph on first use and replayed on later calls with
- * the same grids, parities and nsteps.  Work items (step, stage phase,
- * instance, tile) are taken in order by resident CTAs; a per-instance
- * completion count orders the phases of each instance.  Each tile is 32 x 8
- * points by tz planes, tz chosen per grid shape by osb_autotune (default 4).
+ * 3.3 solver) by nsteps RK3 steps each.  Two ways, chosen by precision
+ * (environment OSB_BATCH_MODE = persistent | streams | phases overrides):
+ *  - FP64 (default "persistent"): ONE persistent kernel launch for all steps,
+ *    captured into a CUDA graph on first use and replayed on later calls with
+ *    the same grids, parities and nsteps.  Work items (step, stage phase,
+ *    instance, tile) are taken in order by resident CTAs; a per-instance
+ *    completion count orders the phases of each instance.  Each tile is 32 x 8
+ *    points by tz planes, tz chosen per grid shape by osb_autotune (default 4).
+ *  - FP32 and double-float (default "streams"): each grid's own one-step CUDA
+ *    graph (the kernels osb_rk3_step runs) replayed step by step on one of up
+ *    to 8 library-owned streams (grids spread over them by size, largest
+ *    first), so small grids run side by side; the streams wait for earlier
+ *    work on the grids' stream and the grids' stream waits for them.
+ *  - "phases" (double-float only): one launch per sub-step of every RK stage
+ *    over the tiles of all grids.
  * Requirements: 1 <= n <= 128 distinct grids on one stream with the same
  * order, precision and viscous form (else OSB_ERR_INVALID_ARG /
- * OSB_ERR_UNSUPPORTED).  Synchronises the stream (it reads the status word).
- * OSB_ERR_TIMEOUT: a device-side wait exceeded its limit (osb_batch_configure);
- * the kernel stopped and the grids' states are undefined, the CUDA context
- * stays usable.  Results equal those of osb_rk3_step on each grid. */
+ * OSB_ERR_UNSUPPORTED).  Synchronises the stream.
+ * OSB_ERR_TIMEOUT (persistent kernel only): a device-side wait exceeded its
+ * limit (osb_batch_configure); the kernel stopped and the grids' states are
+ * undefined, the CUDA context stays usable.  Results equal those of
+ * osb_rk3_step on each grid (bit for bit in FP64 and in the stream mode; FP32
+ * work items of the persistent kernel to FP32 rounding). */
 osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps);
 
 /* Ensemble controls (tooling; no counterpart in the paper).  wait_limit_seconds
- * bounds every per-instance wait of osb_batch_step (default 2 s; must be in
+ * bounds every per-instance wait of osb_batch_step's persistent kernel
+ * (default 2 s; must be in
  * (0, 3600]).  test_stall != 0 makes the first wait of the next batches target
  * a count that nothing reaches, so the wait runs out and the call returns
- * OSB_ERR_TIMEOUT -- used to test the failure path without faulting a GPU.
+ * OSB_ERR_TIMEOUT -- used to test the failure path without faulting a GPU
+ * (while set, every ensemble runs the persistent kernel).
  * Process-wide settings. */
 osb_status osb_batch_configure(double wait_limit_seconds, int test_stall);
 
-/* Times osb_batch_step on this grid alone for each candidate tile depth
+/* Times osb_batch_step's persistent kernel on this grid alone for each candidate tile depth
  * (1, 2, 4, 8, 16 z planes), trial_steps steps each, and keeps the fastest for
  * the grid's shape (nx, ny, nz, order, precision, form) in a process-wide table,
  * also written to the file named by $OSB_AUTOTUNE_CACHE when set (read back

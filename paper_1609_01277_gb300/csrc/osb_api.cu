@@ -30,6 +30,15 @@ struct NvtxRange {
 const char *const kStageRange[3] = {"osb rk3 stage 1", "osb rk3 stage 2", "osb rk3 stage 3"};
 }  // namespace
 
+// Streams of the concurrent-stream ensemble mode: the instances' per-grid
+// step graphs are replayed on up to kBatchStreams streams (the default number
+// of hardware work queues: more streams would share them).
+constexpr int kBatchStreams = 8;
+struct BatchStreams {
+    cudaStream_t s[kBatchStreams];
+    cudaEvent_t ev[kBatchStreams + 1];  // ev[j]: stream j done; ev[kBatchStreams]: fork
+};
+
 struct osb_grid {
     osb_grid_desc desc;
     osb_params prm;
@@ -67,6 +76,9 @@ struct osb_grid {
     char *batch_ctl;
     std::map<std::string, cudaGraphExec_t> *graphs;
     cudaStream_t capture_st;  // library-owned stream the batch graphs are captured on
+    // ensemble stepping on concurrent streams (lead grid only): library-owned
+    // streams and their fork/join events, or nullptr
+    struct BatchStreams *bstreams;
     osb_closure *closure;     // learned correction added to R in every stage, or nullptr
     // FP32 z-march stage: TMA descriptors per stage source q[b] (b = 0, 1)
     zm::ZTma *ztma;           // [2 sources][flux, rhs]
@@ -524,6 +536,14 @@ osb_status osb_grid_destroy(osb_grid *g) {
         delete g->graphs;
     }
     if (g->capture_st) cudaStreamDestroy(g->capture_st);
+    if (g->bstreams) {
+        for (int j = 0; j < kBatchStreams; ++j) {
+            if (g->bstreams->s[j]) cudaStreamDestroy(g->bstreams->s[j]);
+            if (g->bstreams->ev[j]) cudaEventDestroy(g->bstreams->ev[j]);
+        }
+        if (g->bstreams->ev[kBatchStreams]) cudaEventDestroy(g->bstreams->ev[kBatchStreams]);
+        delete g->bstreams;
+    }
     for (int b = 0; b < 2; ++b)
         if (g->step_graph[b]) cudaGraphExecDestroy(g->step_graph[b]);
     delete[] g->ztma;
@@ -1003,7 +1023,103 @@ int tile_depth(const osb_grid_desc &d) {
     return d.precision == OSB_FP32 ? 8 : 4;
 }
 
-osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
+// How an ensemble advances:
+//   BATCH_PERSISTENT: one persistent kernel for all steps (work items with
+//     per-instance completion counts; the only mode with device-side waits);
+//   BATCH_PHASES: one launch per sub-step over all instances (double-float
+//     point items), each sub-step with its own register budget;
+//   BATCH_STREAMS: each instance's per-grid step graph, instances spread over
+//     concurrent library-owned streams: the per-grid kernels (register
+//     budgets, weights from the constant bank, the fused FP32 stage) with the
+//     small grids running side by side instead of one after another.
+// OSB_BATCH_MODE = persistent | phases | streams overrides the default
+// (persistent for FP64, streams for FP32 and double-float: 64 grids of
+// 32^3..128^3 at order 4 measured FP64 1.94e9 / 1.91e9 point-stages/s
+// persistent / streams, FP32 1.47e10 / 2.10e10, double-float 3.93e9 / 5.89e9);
+// the wait-timeout test keeps the persistent kernel.
+enum { BATCH_PERSISTENT = 0, BATCH_PHASES = 1, BATCH_STREAMS = 2 };
+
+static int batch_mode(int precision, bool zmode) {
+    if (g_batch_cfg.test_stall) return BATCH_PERSISTENT;
+    int m = precision == OSB_FP64 ? BATCH_PERSISTENT : BATCH_STREAMS;
+    if (const char *e = getenv("OSB_BATCH_MODE")) {
+        if (strcmp(e, "persistent") == 0) m = BATCH_PERSISTENT;
+        if (strcmp(e, "phases") == 0) m = BATCH_PHASES;
+        if (strcmp(e, "streams") == 0) m = BATCH_STREAMS;
+    }
+    if (m == BATCH_PHASES && (zmode || precision != OSB_DF64)) m = BATCH_PERSISTENT;
+    return m;
+}
+
+// BATCH_STREAMS: instances go, largest first, to the least-loaded of up to
+// kBatchStreams streams; each stream replays its instances' step graphs step
+// by step (an instance's steps stay in order on its stream); fork and join
+// events tie the streams to the grids' stream before and after.
+static osb_status batch_streams(osb_grid *const *grids, int n, int nsteps) {
+    osb_grid *lead = grids[0];
+    cudaStream_t st = lead->st;
+    if (!lead->bstreams) {
+        BatchStreams *b = new (std::nothrow) BatchStreams;
+        if (!b) return fail(OSB_ERR_INVALID_ARG, "batch: host allocation failed");
+        memset(b, 0, sizeof(*b));
+        lead->bstreams = b;
+        for (int j = 0; j < kBatchStreams; ++j) {
+            cudaError_t e = cudaStreamCreateWithFlags(&b->s[j], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[j], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "batch stream creation");
+        }
+        cudaError_t e = cudaEventCreateWithFlags(&b->ev[kBatchStreams], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "batch event creation");
+    }
+    BatchStreams &B = *lead->bstreams;
+    const int K = n < kBatchStreams ? n : kBatchStreams;
+    std::vector<int> order(n), home(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return grids[a]->d.n > grids[b]->d.n; });
+    std::vector<long long> load(K, 0);
+    for (int i : order) {
+        int j = 0;
+        for (int q = 1; q < K; ++q)
+            if (load[q] < load[j]) j = q;
+        home[i] = j;
+        load[j] += grids[i]->d.n;
+    }
+    for (int i = 0; i < n; ++i) {
+        osb_status s0 = ensure_stage_copy(grids[i]);
+        if (s0 != OSB_OK) return s0;
+    }
+    cudaError_t e = cudaEventRecord(B.ev[kBatchStreams], st);
+    for (int j = 0; j < K && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(B.s[j], B.ev[kBatchStreams], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+    std::vector<int> cur(n);
+    for (int i = 0; i < n; ++i) cur[i] = grids[i]->cur;
+    for (int s = 0; s < nsteps; ++s)
+        for (int i : order) {
+            cudaGraphExec_t ge = nullptr;
+            osb_status s0 = step_graph(grids[i], cur[i], &ge);
+            if (s0 != OSB_OK) return s0;
+            e = cudaGraphLaunch(ge, B.s[home[i]]);
+            if (e != cudaSuccess) return cuda_fail(e, "batch step graph launch");
+            cur[i] = 1 - cur[i];
+        }
+    for (int j = 0; j < K && e == cudaSuccess; ++j) {
+        e = cudaEventRecord(B.ev[j], B.s[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B.ev[j], 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch join");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "batch sync");
+    for (int i = 0; i < n; ++i) {
+        osb_grid *g = grids[i];
+        g->cur = cur[i];
+        g->qc = g->cur;
+        g->step += nsteps;
+        g->t = g->step * g->prm.dt;
+    }
+    return OSB_OK;
+}
+
+osb_status batch_run(osb_grid *const *grids, int n, int nsteps, int force_mode = -1) {
     if (!grids || n < 1 || n > MAXB || nsteps < 0) return fail(OSB_ERR_INVALID_ARG, "batch: need 1..128 grids, nsteps >= 0");
     for (int i = 0; i < n; ++i) {
         if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
@@ -1027,10 +1143,14 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     // must be 16-byte aligned: x extents multiples of 4)
     bool zmode = g0->desc.precision == OSB_FP32 && g0->desc.visc_form == OSB_VISC_A && g0->desc.order <= 8;
     for (int i = 0; i < n && zmode; ++i) zmode = grids[i]->zmarch && grids[i]->d.nx % 4 == 0;
+    const int mode = force_mode >= 0 ? force_mode : batch_mode(g0->desc.precision, zmode);
+    if (mode == BATCH_STREAMS) return batch_streams(grids, n, nsteps);
+    const bool phased = mode == BATCH_PHASES;
     BatchParams P;
     memset(&P, 0, sizeof(P));
     P.n = n;
     P.phases = zmode ? 6 : 9;
+    P.pprefix[0] = 0;
     P.prefix[0] = 0;
     std::string key = std::to_string(nsteps) + "|" + std::to_string(g_batch_cfg.test_stall) + "|" +
                       std::to_string((long long)(g_batch_cfg.wait_limit_s * 1e9));
@@ -1067,6 +1187,9 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
         const long long tiles = (long long)rec.tiles_x * rec.tiles_y * rec.tiles_z;
         if (P.prefix[i] + tiles > 0x3fffffff) return fail(OSB_ERR_INVALID_ARG, "batch too large");
         P.prefix[i + 1] = P.prefix[i] + (int)tiles;
+        const long long ptiles = (long long)rec.tiles_x * rec.tiles_y * ((g->d.nz + kPhaseZP - 1) / kPhaseZP);
+        if (P.pprefix[i] + ptiles > 0x7fffffff) return fail(OSB_ERR_INVALID_ARG, "batch too large");
+        P.pprefix[i + 1] = P.pprefix[i] + (int)ptiles;
         P.rec[i] = g->batch_rec;
         P.p0[i] = g->cur;
         char b[64];
@@ -1086,7 +1209,8 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     P.err = (int *)(ctl + 8);
     P.done = (unsigned *)(ctl + 16);
 
-    // one memset and one persistent launch, captured once per (grids, parity,
+    // one memset and one persistent launch (per-phase mode: three launches per
+    // RK stage of every step), captured once per (grids, parity,
     // nsteps) and replayed as a CUDA graph
     osb_grid *lead = grids[0];
     if (!lead->graphs) lead->graphs = new std::map<std::string, cudaGraphExec_t>();
@@ -1097,7 +1221,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
     // graph
     key.append(reinterpret_cast<const char *>(&P), sizeof(P));
     key += "|" + std::to_string(g0->desc.order) + ":" + std::to_string(g0->desc.precision) + ":" +
-           std::to_string(g0->desc.visc_form) + ":" + std::to_string((int)zmode);
+           std::to_string(g0->desc.visc_form) + ":" + std::to_string((int)zmode) + ":" + std::to_string((int)phased);
     auto it = lead->graphs->find(key);
     if (it != lead->graphs->end()) {
         exec = it->second;
@@ -1117,7 +1241,17 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps) {
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
         cudaError_t e1 = cudaMemsetAsync(ctl, 0, 16 + sizeof(unsigned) * MAXB, cs);
-        cudaError_t e2 = launch_batch(P, g0->desc.order, g0->desc.precision, g0->desc.visc_form, (int)zmode, cs);
+        cudaError_t e2 = cudaSuccess;
+        if (phased) {
+            for (int s = 0; s < nsteps && e2 == cudaSuccess; ++s)
+                for (int k = 0; k < 3 && e2 == cudaSuccess; ++k) {
+                    P.step = s;
+                    P.stage = k;
+                    e2 = launch_batch_phase(P, g0->desc.order, g0->desc.visc_form, cs);
+                }
+        } else {
+            e2 = launch_batch(P, g0->desc.order, g0->desc.precision, g0->desc.visc_form, (int)zmode, cs);
+        }
         e = cudaStreamEndCapture(cs, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -1273,10 +1407,10 @@ osb_status osb_autotune(osb_grid *g, int trial_steps, int *best_tz) {
             (*g_tune)[key] = tz;
         }
         osb_grid *one[1] = {g};
-        s = batch_run(one, 1, 1);  // warm-up (captures the graph)
+        s = batch_run(one, 1, 1, BATCH_PERSISTENT);  // warm-up (captures the graph); tile depths are the persistent kernel's
         if (s != OSB_OK) break;
         cudaEventRecord(e0, g->st);
-        s = batch_run(one, 1, trial_steps);
+        s = batch_run(one, 1, trial_steps, BATCH_PERSISTENT);
         cudaEventRecord(e1, g->st);
         if (s != OSB_OK) break;
         cudaEventSynchronize(e1);

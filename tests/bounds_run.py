@@ -98,8 +98,10 @@ def main() -> int:
                 g.stage(k)
         for w, g in enumerate(grids):
             out[f"slab_{tag}_{w}"] = status(g)
-    # ensembles: three-kernel items (FP64) and z-march items (FP32)
-    for prec, tag in ((F64, "fp64"), (F32, "fp32")):
+    # ensembles: three-kernel items (FP64) and z-march items (FP32) of the
+    # persistent kernel, FP32 step graphs on concurrent streams
+    for prec, tag, mode in ((F64, "fp64", "persistent"), (F32, "fp32", "persistent"), (F32, "fp32s", "streams")):
+        os.environ["OSB_BATCH_MODE"] = mode
         ens = []
         for i, n in enumerate((12, 20, 16)):
             g = osb.Grid(osb.Config(n, n, n, order=4, precision=prec, dt=1e-3))
@@ -108,6 +110,7 @@ def main() -> int:
         osb.batch_step(ens, 2)
         for i, g in enumerate(ens):
             out[f"batch_{tag}_{i}"] = status(g)
+    os.environ.pop("OSB_BATCH_MODE", None)
     g = run("parity_fp64_o4_13x11x9", 13, 11, 9, 4, steps=3)
     out["_state"] = g.get_state().tolist()
     print(json.dumps(out))

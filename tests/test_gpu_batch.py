@@ -25,6 +25,13 @@ def osb():
     return m
 
 
+@pytest.fixture(autouse=True)
+def persistent_kernel(monkeypatch):
+    """These tests cover the persistent kernel's work items unless a test
+    picks another mode itself (FP32 ensembles default to the stream mode)."""
+    monkeypatch.setenv("OSB_BATCH_MODE", "persistent")
+
+
 def _ensemble(osb, specs, precision, order=4, seed=3):
     grids = []
     for i, (n, Re, M, dt) in enumerate(specs):
@@ -260,3 +267,22 @@ def test_autotune_fp32_candidates(osb):
     tz = osb.autotune(g, trial_steps=2)
     assert tz in (4, 8, 16, 32)
     assert np.array_equal(g.get_state(), before)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_stream_mode_equals_per_grid_steps_bitwise(osb, monkeypatch, precision):
+    """OSB_BATCH_MODE=streams replays each grid's own step graph on one of the
+    library's concurrent streams: bit for bit the per-grid steps, over calls
+    with odd and even step counts (the grids' register roles flip)."""
+    prec = osb.OSB_FP64 if precision == "fp64" else osb.OSB_FP32
+    a = _ensemble(osb, SPECS, prec)
+    b = _ensemble(osb, SPECS, prec)
+    for g in a:
+        g.step(6)
+    monkeypatch.setenv("OSB_BATCH_MODE", "streams")
+    osb.batch_step(b, 1)
+    osb.batch_step(b, 3)
+    osb.batch_step(b, 2)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.get_state(), gb.get_state())
+

@@ -128,7 +128,7 @@ def test_df64_graph_replay_equals_direct_launches(osb, monkeypatch):
 
 
 def test_df64_ensemble_equals_per_grid_steps(osb):
-    """The persistent ensemble kernel runs the same double-float stage code."""
+    """The ensemble's per-phase launches run the same double-float stage code."""
     specs = [(16, 800.0, 2e-3), (20, 1600.0, 1e-3), (12, 300.0, 3e-3)]
     a, b = [], []
     for i, (n, Re, dt) in enumerate(specs):
@@ -145,3 +145,32 @@ def test_df64_ensemble_equals_per_grid_steps(osb):
         Qo = orc.rk3_step(case, orc.tgv_init(case, inputs.gaussian_noise(n, n, n, 60 + i), 1e-3), 3)
         for m, err in rel_l2_fields(B, Qo).items():
             assert err < TOL, (m, err)
+
+
+@pytest.mark.parametrize("mode", ["phases", "streams"])
+def test_df64_ensemble_modes_match_persistent_kernel(osb, monkeypatch, mode):
+    """Per-phase launches and concurrent-stream step graphs against the
+    persistent kernel (OSB_BATCH_MODE) on uneven grids, ragged in y (extents
+    not multiples of the 8-row tile), over two calls with different parities;
+    the stream mode replays the per-grid step graphs, so it also equals
+    per-grid stepping bit for bit."""
+    specs = [(16, 800.0, 2e-3), (20, 1600.0, 1e-3), (12, 300.0, 3e-3), (28, 500.0, 1.5e-3)]
+    runs = []
+    for m in ("persistent", mode, "single"):
+        monkeypatch.setenv("OSB_BATCH_MODE", m)
+        gs = []
+        for i, (n, Re, dt) in enumerate(specs):
+            g = _grid(osb, n, n + 2, n, order=4, Re=Re, dt=dt)
+            g.init_taylor_green(inputs.gaussian_noise(n, n + 2, n, 80 + i), 1e-3)
+            gs.append(g)
+        if m == "single":
+            for g in gs:
+                g.step(5)
+        else:
+            osb.batch_step(gs, 3)
+            osb.batch_step(gs, 2)
+        runs.append([g.get_state() for g in gs])
+    for A, B, C in zip(*runs):
+        assert np.max(np.abs(A - B)) <= 1e-13 * np.max(np.abs(A))
+        if mode == "streams":
+            assert np.array_equal(B, C)
