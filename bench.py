@@ -340,19 +340,14 @@ def run_ensemble(torch, osb, inputs, steps, precision):
 
 def ensemble_launches(precision, count):
     """How the library runs an ensemble step (OSB_BATCH_MODE overrides the
-    default): FP64 and FP32 in one persistent launch for all steps;
-    double-float as each grid's own step graph (9 kernels) replayed on 8
+    default): FP64 in one persistent launch for all steps; FP32 and
+    double-float as each grid's own step graph (3 or 9 kernels) replayed on 8
     concurrent library streams, the grids spread over them by points."""
-    mode = os.environ.get("OSB_BATCH_MODE") or ("streams" if precision == "df64" else "persistent")
-    if mode == "phases" and precision != "df64":
-        mode = "persistent"
+    mode = os.environ.get("OSB_BATCH_MODE") or ("persistent" if precision == "fp64" else "streams")
     per_grid = (3 if precision == "fp32" else 9) * count
     if mode == "streams":
         return {"mode": "streams", "launches_per_step": f"{count} step graphs ({per_grid} kernels) on 8 streams",
                 "per_grid_launches_per_step": per_grid, "items": "per-grid step graphs"}
-    if mode == "phases":
-        return {"mode": "phases", "launches_per_step": 9, "per_grid_launches_per_step": per_grid,
-                "items": "per-phase launches of three-kernel point items"}
     return {"mode": "persistent", "launches_per_step": "1 persistent launch for all steps",
             "per_grid_launches_per_step": (6 if precision == "fp32" else 9) * count,
             "items": "z-march column items" if precision == "fp32" else "three-kernel point items"}

@@ -211,7 +211,7 @@ osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
 /* Advances n independent grids (an ensemble of uneven sizes, Reynolds and
  * Mach numbers and time steps; an extension of the paper's Section
  * 3.3 solver) by nsteps RK3 steps each.  Two ways, chosen by precision
- * (environment OSB_BATCH_MODE = persistent | streams | phases overrides):
+ * (environment OSB_BATCH_MODE = persistent | streams overrides):
  *  - FP64 (default "persistent"): ONE persistent kernel launch for all steps,
  *    captured into a CUDA graph on first use and replayed on later calls with
  *    the same grids, parities and nsteps.  Work items (step, stage phase,
@@ -223,8 +223,6 @@ osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
  *    to 8 library-owned streams (grids spread over them by size, largest
  *    first), so small grids run side by side; the streams wait for earlier
  *    work on the grids' stream and the grids' stream waits for them.
- *  - "phases" (double-float only): one launch per sub-step of every RK stage
- *    over the tiles of all grids.
  * Requirements: 1 <= n <= 128 distinct grids on one stream with the same
  * order, precision and viscous form (else OSB_ERR_INVALID_ARG /
  * OSB_ERR_UNSUPPORTED).  Synchronises the stream.

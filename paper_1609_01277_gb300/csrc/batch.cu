@@ -270,16 +270,4 @@ cudaError_t launch_batch(const BatchParams &P, int order, int precision, int vis
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_batch_phase(const BatchParams &P, int order, int visc_form, cudaStream_t st) {
-    switch (order / 2) {
-        case 1: return launch_batch_phase_r1(P, visc_form, st);
-        case 2: return launch_batch_phase_r2(P, visc_form, st);
-        case 3: return launch_batch_phase_r3(P, visc_form, st);
-        case 4: return launch_batch_phase_r4(P, visc_form, st);
-        case 5: return launch_batch_phase_r5(P, visc_form, st);
-        case 6: return launch_batch_phase_r6(P, visc_form, st);
-    }
-    return cudaErrorInvalidValue;
-}
-
 }  // namespace osb

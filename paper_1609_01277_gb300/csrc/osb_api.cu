@@ -1026,28 +1026,24 @@ int tile_depth(const osb_grid_desc &d) {
 // How an ensemble advances:
 //   BATCH_PERSISTENT: one persistent kernel for all steps (work items with
 //     per-instance completion counts; the only mode with device-side waits);
-//   BATCH_PHASES: one launch per sub-step over all instances (double-float
-//     point items), each sub-step with its own register budget;
 //   BATCH_STREAMS: each instance's per-grid step graph, instances spread over
 //     concurrent library-owned streams: the per-grid kernels (register
 //     budgets, weights from the constant bank, the fused FP32 stage) with the
 //     small grids running side by side instead of one after another.
-// OSB_BATCH_MODE = persistent | phases | streams overrides the default
+// OSB_BATCH_MODE = persistent | streams overrides the default
 // (persistent for FP64, streams for FP32 and double-float: 64 grids of
 // 32^3..128^3 at order 4 measured FP64 1.94e9 / 1.91e9 point-stages/s
 // persistent / streams, FP32 1.47e10 / 2.10e10, double-float 3.93e9 / 5.89e9);
 // the wait-timeout test keeps the persistent kernel.
-enum { BATCH_PERSISTENT = 0, BATCH_PHASES = 1, BATCH_STREAMS = 2 };
+enum { BATCH_PERSISTENT = 0, BATCH_STREAMS = 1 };
 
 static int batch_mode(int precision, bool zmode) {
     if (g_batch_cfg.test_stall) return BATCH_PERSISTENT;
     int m = precision == OSB_FP64 ? BATCH_PERSISTENT : BATCH_STREAMS;
     if (const char *e = getenv("OSB_BATCH_MODE")) {
         if (strcmp(e, "persistent") == 0) m = BATCH_PERSISTENT;
-        if (strcmp(e, "phases") == 0) m = BATCH_PHASES;
         if (strcmp(e, "streams") == 0) m = BATCH_STREAMS;
     }
-    if (m == BATCH_PHASES && (zmode || precision != OSB_DF64)) m = BATCH_PERSISTENT;
     return m;
 }
 
@@ -1145,12 +1141,10 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps, int force_mode =
     for (int i = 0; i < n && zmode; ++i) zmode = grids[i]->zmarch && grids[i]->d.nx % 4 == 0;
     const int mode = force_mode >= 0 ? force_mode : batch_mode(g0->desc.precision, zmode);
     if (mode == BATCH_STREAMS) return batch_streams(grids, n, nsteps);
-    const bool phased = mode == BATCH_PHASES;
     BatchParams P;
     memset(&P, 0, sizeof(P));
     P.n = n;
     P.phases = zmode ? 6 : 9;
-    P.pprefix[0] = 0;
     P.prefix[0] = 0;
     std::string key = std::to_string(nsteps) + "|" + std::to_string(g_batch_cfg.test_stall) + "|" +
                       std::to_string((long long)(g_batch_cfg.wait_limit_s * 1e9));
@@ -1187,9 +1181,6 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps, int force_mode =
         const long long tiles = (long long)rec.tiles_x * rec.tiles_y * rec.tiles_z;
         if (P.prefix[i] + tiles > 0x3fffffff) return fail(OSB_ERR_INVALID_ARG, "batch too large");
         P.prefix[i + 1] = P.prefix[i] + (int)tiles;
-        const long long ptiles = (long long)rec.tiles_x * rec.tiles_y * ((g->d.nz + kPhaseZP - 1) / kPhaseZP);
-        if (P.pprefix[i] + ptiles > 0x7fffffff) return fail(OSB_ERR_INVALID_ARG, "batch too large");
-        P.pprefix[i + 1] = P.pprefix[i] + (int)ptiles;
         P.rec[i] = g->batch_rec;
         P.p0[i] = g->cur;
         char b[64];
@@ -1209,8 +1200,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps, int force_mode =
     P.err = (int *)(ctl + 8);
     P.done = (unsigned *)(ctl + 16);
 
-    // one memset and one persistent launch (per-phase mode: three launches per
-    // RK stage of every step), captured once per (grids, parity,
+    // one memset and one persistent launch, captured once per (grids, parity,
     // nsteps) and replayed as a CUDA graph
     osb_grid *lead = grids[0];
     if (!lead->graphs) lead->graphs = new std::map<std::string, cudaGraphExec_t>();
@@ -1221,7 +1211,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps, int force_mode =
     // graph
     key.append(reinterpret_cast<const char *>(&P), sizeof(P));
     key += "|" + std::to_string(g0->desc.order) + ":" + std::to_string(g0->desc.precision) + ":" +
-           std::to_string(g0->desc.visc_form) + ":" + std::to_string((int)zmode) + ":" + std::to_string((int)phased);
+           std::to_string(g0->desc.visc_form) + ":" + std::to_string((int)zmode);
     auto it = lead->graphs->find(key);
     if (it != lead->graphs->end()) {
         exec = it->second;
@@ -1241,17 +1231,7 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps, int force_mode =
         cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
         cudaError_t e1 = cudaMemsetAsync(ctl, 0, 16 + sizeof(unsigned) * MAXB, cs);
-        cudaError_t e2 = cudaSuccess;
-        if (phased) {
-            for (int s = 0; s < nsteps && e2 == cudaSuccess; ++s)
-                for (int k = 0; k < 3 && e2 == cudaSuccess; ++k) {
-                    P.step = s;
-                    P.stage = k;
-                    e2 = launch_batch_phase(P, g0->desc.order, g0->desc.visc_form, cs);
-                }
-        } else {
-            e2 = launch_batch(P, g0->desc.order, g0->desc.precision, g0->desc.visc_form, (int)zmode, cs);
-        }
+        cudaError_t e2 = launch_batch(P, g0->desc.order, g0->desc.precision, g0->desc.visc_form, (int)zmode, cs);
         e = cudaStreamEndCapture(cs, &graph);
         if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);

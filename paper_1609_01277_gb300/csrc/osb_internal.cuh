@@ -212,8 +212,6 @@ struct BatchInst {
     zm::ZTma tma[2][2];   // FP32 z-march items: [stage register][flux, rhs]
 };
 
-constexpr int kPhaseZP = 4;  // z planes per CTA of the per-phase ensemble launches
-
 struct BatchParams {
     int n;
     int tiles_total;       // items per phase sequence, all instances
@@ -227,23 +225,9 @@ struct BatchParams {
     unsigned long long *counter;
     unsigned *done;
     int *err;
-    // per-phase launches (batch_phase.cuh): block prefix sums (tiles_x *
-    // tiles_y * ceil(nz / kPhaseZP) per instance) and the step and RK stage of
-    // the launch
-    int pprefix[MAXB + 1];
-    int step, stage;
 };
 
 cudaError_t launch_batch(const BatchParams &P, int order, int precision, int visc_form, int zmode, cudaStream_t st);
-// the three sub-step launches of RK stage P.stage of step P.step over every
-// instance (double-float ensembles)
-cudaError_t launch_batch_phase(const BatchParams &P, int order, int visc_form, cudaStream_t st);
-cudaError_t launch_batch_phase_r1(const BatchParams &P, int visc_form, cudaStream_t st);
-cudaError_t launch_batch_phase_r2(const BatchParams &P, int visc_form, cudaStream_t st);
-cudaError_t launch_batch_phase_r3(const BatchParams &P, int visc_form, cudaStream_t st);
-cudaError_t launch_batch_phase_r4(const BatchParams &P, int visc_form, cudaStream_t st);
-cudaError_t launch_batch_phase_r5(const BatchParams &P, int visc_form, cudaStream_t st);
-cudaError_t launch_batch_phase_r6(const BatchParams &P, int visc_form, cudaStream_t st);
 
 // Learned closure (closure.cu).
 namespace cl {

@@ -221,8 +221,9 @@ def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count
                  autotune: bool = True) -> dict:
     """The uneven Taylor-Green ensemble (64 grids of 32^3..128^3, Re in
     [100, 3200], M in [0.05, 0.3], order 4) advanced `steps` RK3 steps by
-    osb_batch_step in chunks of `every` (one persistent launch per chunk),
-    with every grid's E_k after each chunk.  Per precision: time, point-stages
+    osb_batch_step in chunks of `every` (one call per chunk: FP64 one
+    persistent launch, FP32 and double-float the grids' step graphs on
+    concurrent streams), with every grid's E_k after each chunk.  Per precision: time, point-stages
     per second; FP32 against FP64: the KE-decay error max over grids and
     chunks of |E_k - E_k^FP64| / E_k^FP64(0), and the speed-up."""
     import torch
@@ -239,7 +240,8 @@ def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count
             g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
             grids.append(g)
         tuned = {}
-        for g in grids if autotune else []:
+        mode = os.environ.get("OSB_BATCH_MODE") or ("persistent" if precision == "fp64" else "streams")
+        for g in grids if autotune and mode == "persistent" else []:  # tile depths of the persistent kernel
             if g.cfg.nx not in tuned:
                 tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
         for i, g in enumerate(grids):  # autotuning stepped the grids: start again

@@ -147,9 +147,9 @@ def test_df64_ensemble_equals_per_grid_steps(osb):
             assert err < TOL, (m, err)
 
 
-@pytest.mark.parametrize("mode", ["phases", "streams"])
+@pytest.mark.parametrize("mode", ["streams"])
 def test_df64_ensemble_modes_match_persistent_kernel(osb, monkeypatch, mode):
-    """Per-phase launches and concurrent-stream step graphs against the
+    """Concurrent-stream step graphs (the double-float default) against the
     persistent kernel (OSB_BATCH_MODE) on uneven grids, ragged in y (extents
     not multiples of the 8-row tile), over two calls with different parities;
     the stream mode replays the per-grid step graphs, so it also equals
