@@ -70,6 +70,24 @@ def test_sizes(osb):
     assert L.osb_workspace_bytes(ctypes.byref(bad)) == 0
 
 
+def test_point_count_bound(osb):
+    """Grids hold at most 2^31 - 1 points (the point count is a 32-bit int in
+    the kernels' index arithmetic; their grid-stride loops run in 64 bits, so
+    the last stride past n cannot wrap): 1 x 1 x (2^31 - 1) is sized, one
+    point more is refused by every size query."""
+    L = osb.load()
+    top = (1 << 31) - 1
+    ok = osb.GridDesc(1, 1, top, 2, osb.OSB_FP64, 0)
+    sb = L.osb_state_bytes(ctypes.byref(ok))
+    assert sb >= 20 * top * 8 and sb - 20 * top * 8 < 20 * 256
+    assert L.osb_workspace_bytes(ctypes.byref(ok)) > 0
+    for dims in ((1, 1, 1 << 31), (2, 1 << 15, 1 << 15), (46341, 46341, 1)):
+        over = osb.GridDesc(*dims, 2, osb.OSB_FP64, 0)
+        assert dims[0] * dims[1] * dims[2] > top
+        assert L.osb_state_bytes(ctypes.byref(over)) == 0
+        assert L.osb_workspace_bytes(ctypes.byref(over)) == 0
+
+
 @pytest.mark.parametrize("desc", [
     (0, 8, 8, 4, 0, 0), (8, 8, 8, 3, 0, 0), (8, 8, 8, 14, 0, 0), (8, 8, 8, 0, 0, 0),
     (8, 8, 8, 4, 3, 0), (8, 8, 8, 4, 0, 7), (2048, 2048, 1024, 4, 0, 0)])
