@@ -340,10 +340,11 @@ def run_ensemble(torch, osb, inputs, steps, precision):
 
 def ensemble_launches(precision, count):
     """How the library runs an ensemble step (OSB_BATCH_MODE overrides the
-    default): FP64 in one persistent launch for all steps; FP32 and
-    double-float as each grid's own step graph (3 or 9 kernels) replayed on 8
-    concurrent library streams, the grids spread over them by points."""
-    mode = os.environ.get("OSB_BATCH_MODE") or ("persistent" if precision == "fp64" else "streams")
+    default): FP64 and FP32 in one persistent launch for all steps;
+    double-float as each grid's own step graph (9 kernels; 3 for FP32 on
+    request) replayed on 8 concurrent library streams, the grids spread over
+    them by points."""
+    mode = os.environ.get("OSB_BATCH_MODE") or ("streams" if precision == "df64" else "persistent")
     per_grid = (3 if precision == "fp32" else 9) * count
     if mode == "streams":
         return {"mode": "streams", "launches_per_step": f"{count} step graphs ({per_grid} kernels) on 8 streams",
@@ -536,6 +537,21 @@ def run_ours(args):
         edd = variants["ensemble64_order4_df64"]
         edd["speedup_vs_fp64_ensemble"] = edd["value"] / e64["value"]
         edd["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(edd["ke_first4"], e64["ke_first4"]))
+        # FP32 grids' own step graphs (fused stage) on concurrent streams, beside
+        # the persistent launch of the stated configuration
+        prev = os.environ.get("OSB_BATCH_MODE")
+        os.environ["OSB_BATCH_MODE"] = "streams"
+        try:
+            es = run_ensemble(torch, osb, inputs, args.ensemble_steps, "fp32")
+        finally:
+            if prev is None:
+                os.environ.pop("OSB_BATCH_MODE", None)
+            else:
+                os.environ["OSB_BATCH_MODE"] = prev
+        es["speedup_vs_fp64_ensemble"] = es["value"] / e64["value"]
+        es["speedup_vs_persistent_fp32"] = es["value"] / e32["value"]
+        es["ke_err_vs_fp64_first4"] = max(abs(a - b) / b for a, b in zip(es["ke_first4"], e64["ke_first4"]))
+        variants["ensemble64_order4_fp32_streams"] = es
 
     if not args.no_variants and world == 1:
         # viscous-work form B (product rule) and forward Euler, FP64 order 4
@@ -659,8 +675,9 @@ def summarize_variants(variants):
         if name.startswith("order") or name.startswith("euler") or name.startswith("tgv_"):
             out[name] = {k: v[k] for k in keys if k in v and v[k] is not None}
         elif name.startswith("ensemble"):
-            out[name] = {k: v[k] for k in ("value", "ms_per_step", "steps", "speedup_vs_per_grid_launches",
-                                           "speedup_vs_fp64_ensemble", "ke_err_vs_fp64_first4") if k in v}
+            out[name] = {k: v[k] for k in ("value", "ms_per_step", "steps", "mode", "speedup_vs_per_grid_launches",
+                                           "speedup_vs_fp64_ensemble", "speedup_vs_persistent_fp32",
+                                           "ke_err_vs_fp64_first4") if k in v}
         elif name.startswith("scalar"):
             out[name] = {k: v[k] for k in ("value", "fp64_frac") if k in v}
         elif name.startswith("closure") and "summary" in v:

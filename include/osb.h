@@ -212,13 +212,13 @@ osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
  * Mach numbers and time steps; an extension of the paper's Section
  * 3.3 solver) by nsteps RK3 steps each.  Two ways, chosen by precision
  * (environment OSB_BATCH_MODE = persistent | streams overrides):
- *  - FP64 (default "persistent"): ONE persistent kernel launch for all steps,
+ *  - FP64 and FP32 (default "persistent"): ONE persistent kernel launch for all steps,
  *    captured into a CUDA graph on first use and replayed on later calls with
  *    the same grids, parities and nsteps.  Work items (step, stage phase,
  *    instance, tile) are taken in order by resident CTAs; a per-instance
  *    completion count orders the phases of each instance.  Each tile is 32 x 8
  *    points by tz planes, tz chosen per grid shape by osb_autotune (default 4).
- *  - FP32 and double-float (default "streams"): each grid's own one-step CUDA
+ *  - double-float (default "streams"; FP32 on request): each grid's own one-step CUDA
  *    graph (the kernels osb_rk3_step runs) replayed step by step on one of up
  *    to 8 library-owned streams (grids spread over them by size, largest
  *    first), so small grids run side by side; the streams wait for earlier

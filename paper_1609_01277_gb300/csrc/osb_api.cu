@@ -1030,16 +1030,16 @@ int tile_depth(const osb_grid_desc &d) {
 //     concurrent library-owned streams: the per-grid kernels (register
 //     budgets, weights from the constant bank, the fused FP32 stage) with the
 //     small grids running side by side instead of one after another.
-// OSB_BATCH_MODE = persistent | streams overrides the default
-// (persistent for FP64, streams for FP32 and double-float: 64 grids of
-// 32^3..128^3 at order 4 measured FP64 1.94e9 / 1.91e9 point-stages/s
-// persistent / streams, FP32 1.47e10 / 2.10e10, double-float 3.93e9 / 5.89e9);
-// the wait-timeout test keeps the persistent kernel.
+// OSB_BATCH_MODE = persistent | streams overrides the default (persistent for
+// FP64 and FP32, streams for double-float: 64 grids of 32^3..128^3 at order 4
+// measured FP64 1.94e9 / 1.91e9 point-stages/s persistent / streams, FP32
+// 1.47e10 / 2.10e10, double-float 3.93e9 / 5.89e9); the wait-timeout test
+// keeps the persistent kernel.
 enum { BATCH_PERSISTENT = 0, BATCH_STREAMS = 1 };
 
 static int batch_mode(int precision, bool zmode) {
     if (g_batch_cfg.test_stall) return BATCH_PERSISTENT;
-    int m = precision == OSB_FP64 ? BATCH_PERSISTENT : BATCH_STREAMS;
+    int m = precision == OSB_DF64 ? BATCH_STREAMS : BATCH_PERSISTENT;
     if (const char *e = getenv("OSB_BATCH_MODE")) {
         if (strcmp(e, "persistent") == 0) m = BATCH_PERSISTENT;
         if (strcmp(e, "streams") == 0) m = BATCH_STREAMS;

@@ -240,7 +240,7 @@ def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count
             g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
             grids.append(g)
         tuned = {}
-        mode = os.environ.get("OSB_BATCH_MODE") or ("persistent" if precision == "fp64" else "streams")
+        mode = os.environ.get("OSB_BATCH_MODE") or ("streams" if precision == "df64" else "persistent")
         for g in grids if autotune and mode == "persistent" else []:  # tile depths of the persistent kernel
             if g.cfg.nx not in tuned:
                 tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)

@@ -347,9 +347,9 @@ def scalar_rk3(phi, work, order: int, adv=(0.0, 0.0, 0.0), diff: float = 0.0, dt
 
 
 def batch_step(grids, nsteps: int) -> None:
-    """Advances every grid nsteps steps: FP64 in one persistent, graph-captured
-    launch; FP32 and double-float as each grid's step graph on concurrent
-    library streams (OSB_BATCH_MODE overrides)."""
+    """Advances every grid nsteps steps: FP64 and FP32 in one persistent,
+    graph-captured launch; double-float as each grid's step graph on
+    concurrent library streams (OSB_BATCH_MODE overrides)."""
     arr = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
     check(load().osb_batch_step(arr, len(grids), int(nsteps)), "osb_batch_step")
 
