@@ -69,7 +69,6 @@ using zm::smem_u32;
 using zm::tma_load3;
 using zm::wrapz;
 
-constexpr int TX = 32, TY = 8;
 constexpr int NPX = TX / 2;      // x-pairs per tile row
 constexpr int NT = NPX * TY;     // 128 threads
 constexpr int CX = 4;            // x halo columns (>= 2R; row starts stay 16-byte aligned)
@@ -862,7 +861,7 @@ __device__ __forceinline__ void plane_step(Smem<R> &S, const FArgs &a, const FTm
 
 
 template <int R, int MODE, bool DIAG>
-__global__ void __launch_bounds__(NT, 2) k_fused(const __grid_constant__ FArgs a, const __grid_constant__ FTma tm) {
+__global__ void __launch_bounds__(NT, NT <= 128 ? 2 : 1) k_fused(const __grid_constant__ FArgs a, const __grid_constant__ FTma tm) {
     using G = Geo<R>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<R> &S = *reinterpret_cast<Smem<R> *>(smem_raw);

@@ -279,7 +279,7 @@ void build_ztma(osb_grid *g) {
 }
 
 // TMA descriptors of the fused FP32 stage for both stage sources q[0], q[1]:
-// haloed plane boxes of 40 x (8 + 4R) points.  Left unused (cp.async loads)
+// haloed plane boxes of 40 x (TY + 4R) points.  Left unused (cp.async loads)
 // when the x extent is not a multiple of 4 or OSB_FP32_LOADS=cpasync.
 void build_ftma(osb_grid *g) {
     g->ftma = nullptr;
@@ -289,7 +289,7 @@ void build_ftma(osb_grid *g) {
     fz::FTma *t = new (std::nothrow) fz::FTma[2];
     if (!t) return;
     memset(t, 0, 2 * sizeof(fz::FTma));
-    const int eh = 8 + 4 * (g->desc.order / 2);
+    const int eh = fz::TY + 4 * (g->desc.order / 2);
     bool ok = true;
     for (int b = 0; b < 2; ++b) {
         const float *q = (const float *)g->q[b];

@@ -190,7 +190,9 @@ struct ZTma {
 }  // namespace zm
 
 namespace fz {
-// TMA descriptors of the fused stage: haloed plane boxes (40 x (8 + 4R) x 1)
+// Column tile of the fused stage: TX x TY points per CTA, one x-pair per thread.
+constexpr int TX = 32, TY = 8;
+// TMA descriptors of the fused stage: haloed plane boxes (40 x (TY + 4R) x 1)
 // of the five fields of one stencil source.
 struct FTma {
     CUtensorMap q[5];
