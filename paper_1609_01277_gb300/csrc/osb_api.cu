@@ -1087,21 +1087,37 @@ static osb_status batch_streams(osb_grid *const *grids, int n, int nsteps) {
     cudaError_t e = cudaEventRecord(B.ev[kBatchStreams], st);
     for (int j = 0; j < K && e == cudaSuccess; ++j) e = cudaStreamWaitEvent(B.s[j], B.ev[kBatchStreams], 0);
     if (e != cudaSuccess) return cuda_fail(e, "batch fork");
+    // the grids' stream waits for every library stream (also after a failed
+    // launch, so that later work on it cannot overtake what was queued)
+    auto join = [&]() {
+        cudaError_t ej = cudaSuccess;
+        for (int j = 0; j < K; ++j) {
+            cudaError_t r = cudaEventRecord(B.ev[j], B.s[j]);
+            if (r == cudaSuccess) r = cudaStreamWaitEvent(st, B.ev[j], 0);
+            if (ej == cudaSuccess) ej = r;
+        }
+        return ej;
+    };
     std::vector<int> cur(n);
     for (int i = 0; i < n; ++i) cur[i] = grids[i]->cur;
     for (int s = 0; s < nsteps; ++s)
         for (int i : order) {
             cudaGraphExec_t ge = nullptr;
             osb_status s0 = step_graph(grids[i], cur[i], &ge);
-            if (s0 != OSB_OK) return s0;
+            if (s0 != OSB_OK) {
+                join();
+                cudaStreamSynchronize(st);
+                return s0;
+            }
             e = cudaGraphLaunch(ge, B.s[home[i]]);
-            if (e != cudaSuccess) return cuda_fail(e, "batch step graph launch");
+            if (e != cudaSuccess) {
+                join();
+                cudaStreamSynchronize(st);
+                return cuda_fail(e, "batch step graph launch; grid states are undefined");
+            }
             cur[i] = 1 - cur[i];
         }
-    for (int j = 0; j < K && e == cudaSuccess; ++j) {
-        e = cudaEventRecord(B.ev[j], B.s[j]);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, B.ev[j], 0);
-    }
+    e = join();
     if (e != cudaSuccess) return cuda_fail(e, "batch join");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "batch sync");
