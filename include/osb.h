@@ -228,8 +228,10 @@ osb_status osb_diagnostics(osb_grid *grid, osb_diag *out);
  * OSB_ERR_UNSUPPORTED).  Synchronises the stream.
  * OSB_ERR_TIMEOUT (persistent kernel only): a device-side wait exceeded its
  * limit (osb_batch_configure); the kernel stopped and the grids' states are
- * undefined, the CUDA context stays usable.  Results equal those of
- * osb_rk3_step on each grid (bit for bit in FP64 and in the stream mode; FP32
+ * undefined, the CUDA context stays usable.  OSB_ERR_CUDA in the stream mode
+ * (a step graph that could not be captured or launched): the streams are
+ * joined back into the grids' stream and synchronised, and the grids' states
+ * are undefined.  Results equal those of osb_rk3_step on each grid (bit for bit in FP64 and in the stream mode; FP32
  * work items of the persistent kernel to FP32 rounding). */
 osb_status osb_batch_step(osb_grid *const *grids, int n, int nsteps);
 
