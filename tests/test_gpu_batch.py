@@ -286,3 +286,17 @@ def test_batch_stream_mode_equals_per_grid_steps_bitwise(osb, monkeypatch, preci
     for ga, gb in zip(a, b):
         assert np.array_equal(ga.get_state(), gb.get_state())
 
+
+def test_batch_stream_mode_more_grids_than_streams(osb, monkeypatch):
+    """Twelve grids on the 8 library streams (some streams replay several
+    grids' step graphs in turn): bit for bit the per-grid steps."""
+    specs = [(8 + 2 * (i % 5), 200.0 + 150.0 * i, 0.1 + 0.01 * i, 1e-3 + 1e-4 * (i % 3)) for i in range(12)]
+    a = _ensemble(osb, specs, osb.OSB_FP64, seed=40)
+    b = _ensemble(osb, specs, osb.OSB_FP64, seed=40)
+    for g in a:
+        g.step(3)
+    monkeypatch.setenv("OSB_BATCH_MODE", "streams")
+    osb.batch_step(b, 3)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.get_state(), gb.get_state())
+

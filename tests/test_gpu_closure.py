@@ -234,3 +234,26 @@ def test_brick_and_z_marching_tensor_core_kernels_agree(mods, monkeypatch):
     got = c.forward(Qd).cpu().numpy()
     c.status()
     assert _rel(got, ref) < 1e-5
+
+
+@pytest.mark.parametrize("zchunk", ["1", "4"])
+@pytest.mark.parametrize("n", [(8, 16, 4), (24, 16, 4)])
+def test_z_marching_convolutions_on_the_shallowest_grids(mods, monkeypatch, n, zchunk):
+    """Four planes, the fewest a closure grid takes (its bricks are 4 deep):
+    every window wraps in z, and a one-plane chunk loads the same planes into
+    several ring slots.  Forward and gradients against the CPU oracle, and no
+    accumulator wait ran out."""
+    osb, closure, torch = mods
+    c, theta, Q, C, mean, std, out = _setup(mods, n=n, seed=23)
+    Qd, Cd = torch.from_numpy(Q).cuda(), torch.from_numpy(C).cuda()
+    monkeypatch.setenv("OSB_CLOSURE_MMA", "tc")
+    monkeypatch.setenv("OSB_TC_ZCHUNK", zchunk)
+    Cg = c.forward(Qd).cpu().numpy()
+    assert _rel(Cg, co.correction(theta.astype(np.float64), Q, mean, std, out, mode="bf16")) < FWD_TOL
+    loss, grad = c.loss_grad(Qd, Cd)
+    lo, go = co.loss_grad(theta.astype(np.float64), Q, C, mean, std, out, mode="bf16")
+    assert float(loss.item()) == pytest.approx(lo, rel=LOSS_TOL)
+    P, Po = co.unpack(grad.cpu().numpy().astype(np.float64)), co.unpack(go)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert _rel(P[name], Po[name]) < GRAD_TOL, name
+    c.status()
