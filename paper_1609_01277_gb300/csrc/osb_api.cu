@@ -82,6 +82,7 @@ struct osb_grid {
     osb_closure *closure;     // learned correction added to R in every stage, or nullptr
     // FP32 z-march stage: TMA descriptors per stage source q[b] (b = 0, 1)
     zm::ZTma *ztma;           // [2 sources][flux, rhs]
+    zm::ZTmaN *ztman;         // narrow residual kernel (orders 6, 8): [2 sources], or nullptr
     fz::FTma *ftma;           // fused FP32 stage: descriptors per stage source q[b], or nullptr
     int *kerr;                // device error word of bounded in-kernel waits
     cudaGraphExec_t step_graph[2];  // one RK3 step starting with Q^n in U[0] / U[1]
@@ -276,6 +277,30 @@ void build_ztma(osb_grid *g) {
         return;
     }
     g->ztma = t;
+    // the narrow residual kernel of radius 3 and 4: rectangles 40 x (4 + 2R),
+    // columns 32 x 4
+    g->ztman = nullptr;
+    if (g->desc.order < 6) return;
+    zm::ZTmaN *tn = new (std::nothrow) zm::ZTmaN[2];
+    if (!tn) return;
+    memset(tn, 0, 2 * sizeof(zm::ZTmaN));
+    const int rhn = 4 + 2 * (g->desc.order / 2);
+    for (int b = 0; b < 2; ++b) {
+        const float *q = (const float *)g->q[b];
+        const size_t qs = g->q_stride;
+        for (int f = 0; f < 5; ++f) ok = ok && encode_plane_map(&tn[b].rect[f], q + f * qs, g->d, 40, rhn);
+        const int af[4] = {A_FX, A_FY, A_GX, A_GY};
+        for (int f = 0; f < 4; ++f) ok = ok && encode_plane_map(&tn[b].rect[5 + f], aux + af[f] * as, g->d, 40, rhn);
+        for (int f = 0; f < 5; ++f) ok = ok && encode_plane_map(&tn[b].col[f], q + f * qs, g->d, 32, 4);
+        ok = ok && encode_plane_map(&tn[b].col[5], aux + A_FZ * as, g->d, 32, 4);
+        ok = ok && encode_plane_map(&tn[b].col[6], aux + A_GZ * as, g->d, 32, 4);
+        tn[b].use = 1;
+    }
+    if (!ok) {
+        delete[] tn;
+        return;
+    }
+    g->ztman = tn;
 }
 
 // TMA descriptors of the fused FP32 stage for both stage sources q[0], q[1]:
@@ -547,6 +572,7 @@ osb_status osb_grid_destroy(osb_grid *g) {
     for (int b = 0; b < 2; ++b)
         if (g->step_graph[b]) cudaGraphExecDestroy(g->step_graph[b]);
     delete[] g->ztma;
+    delete[] g->ztman;
     delete[] g->ftma;
     delete g->batch_rec_host;
     delete g;
@@ -735,6 +761,7 @@ static StageArgs stage_args(const osb_grid *g, int cur, int k) {
         const int b = (a.src == g->q[0]) ? 0 : 1;
         a.ztma_flux = &g->ztma[2 * b];
         a.ztma_rhs = &g->ztma[2 * b + 1];
+        a.ztma_rhs_n = g->ztman ? &g->ztman[b] : nullptr;
     }
     return a;
 }
@@ -761,7 +788,7 @@ static StageArgs stage_args_fused(const osb_grid *g, int cur, int k) {
     a.U_in = g->U[cur];
     a.U_out = g->U[1 - cur];
     a.u32_out = nullptr;
-    a.ztma_flux = a.ztma_rhs = nullptr;
+    a.ztma_flux = a.ztma_rhs = a.ztma_rhs_n = nullptr;
     if (k == 0) {
         a.src = g->q[qc];
         a.q_out = g->q[1 - qc];
@@ -1178,7 +1205,8 @@ osb_status batch_run(osb_grid *const *grids, int n, int nsteps, int force_mode =
         for (int par = 0; par < 2; ++par)
             for (int k = 0; k < 3; ++k) {
                 rec.st[par][k] = stage_args(g, par, k);
-                rec.st[par][k].ztma_flux = rec.st[par][k].ztma_rhs = nullptr;  // host pointers: not used on the device
+                rec.st[par][k].ztma_flux = rec.st[par][k].ztma_rhs = rec.st[par][k].ztma_rhs_n =
+                    nullptr;  // host pointers: not used on the device
                 rec.st[par][k].diag_rec = nullptr;
                 rec.zsrc[par][k] = (rec.st[par][k].src == g->q[0]) ? 0 : 1;
             }

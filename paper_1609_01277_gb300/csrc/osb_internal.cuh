@@ -138,6 +138,7 @@ struct StageArgs {
     const float *closure;   // learned correction added to R (5 fields, stride d.n), or nullptr
     const void *ztma_flux;  // host: TMA descriptors of the z-march kernels for this stage, or nullptr
     const void *ztma_rhs;
+    const void *ztma_rhs_n; // host: TMA descriptors of the narrow residual kernel (radius 3, 4), or nullptr
     int *kerr;              // device word set when a bounded in-kernel wait ran out
     // per-step diagnostics fused into the first stage (or nullptr): the
     // gradient kernel adds (1/2) rho u.u and (1/2) rho |omega|^2 over each
@@ -185,6 +186,14 @@ namespace zm {
 struct ZTma {
     CUtensorMap rect[9];
     CUtensorMap col[2];
+    int use;
+};
+// The narrow residual kernel of orders 6 and 8 (zrhs_narrow.cuh): haloed
+// rectangles 40 x (4 + 2R) of its nine ring fields (conserved fields, F_x,
+// F_y, g_x, g_y) and 32 x 4 tile columns of the conserved fields, F_z, g_z.
+struct ZTmaN {
+    CUtensorMap rect[9];
+    CUtensorMap col[7];
     int use;
 };
 }  // namespace zm

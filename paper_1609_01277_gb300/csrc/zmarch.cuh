@@ -22,6 +22,8 @@
 
 #include <cuda.h>
 #include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -644,7 +646,22 @@ constexpr size_t rhs_smem() {
     return sizeof(RhsSmem<R>);
 }
 
-// Launches k_zflux then k_zrhs for one RK stage of the FP32 path.
+}  // namespace zm
+}  // namespace osb
+
+#include "zrhs_narrow.cuh"
+
+namespace osb {
+namespace zm {
+
+// The narrow residual kernel for radius 3 and 4 (OSB_FP32_ZRHS=wide: k_zrhs).
+inline bool use_narrow_rhs() {
+    const char *e = getenv("OSB_FP32_ZRHS");
+    return !(e && strcmp(e, "wide") == 0);
+}
+
+// Launches k_zflux then the residual kernel for one RK stage of the FP32
+// path: k_zrhs up to radius 2, k_zrhs_n at radius 3 and 4.
 template <int R>
 cudaError_t launch_zstage(const StageArgs &a) {
     static_assert(R <= 4, "z-march kernels are built for orders up to 8");
@@ -667,6 +684,24 @@ cudaError_t launch_zstage(const StageArgs &a) {
     if (a.ev) cudaEventRecord(a.ev[1], a.stream);  // no separate primitive kernel
     kflux<<<grd, NT, sf, a.stream>>>(a, zchunk, tf);
     if (a.ev) cudaEventRecord(a.ev[2], a.stream);
+    if constexpr (R >= 3) {
+        if (use_narrow_rhs()) {
+            using GN = GeoN<R>;
+            const size_t sn = rhs_smem_n<R>();
+            e = cudaFuncSetAttribute(k_zrhs_n<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sn);
+            if (e != cudaSuccess) return e;
+            // narrow tiles: z chunks for about four CTA rounds of three per SM
+            const int tiles_n = ((a.d.nx + TX - 1) / TX) * ((a.d.ny + GN::TYN - 1) / GN::TYN);
+            int zc = (int)(((long long)a.d.nz * tiles_n + 12 * 152 - 1) / (12 * 152));
+            zc = zc < 4 ? 4 : (zc > 32 ? 32 : zc);
+            dim3 gn((a.d.nx + TX - 1) / TX, (a.d.ny + GN::TYN - 1) / GN::TYN, (a.d.nz + zc - 1) / zc);
+            static const ZTmaN none_n = {};
+            const ZTmaN &tn = a.ztma_rhs_n ? *static_cast<const ZTmaN *>(a.ztma_rhs_n) : none_n;
+            k_zrhs_n<R><<<gn, GN::NTN, sn, a.stream>>>(a, zc, tn);
+            if (a.ev) cudaEventRecord(a.ev[3], a.stream);
+            return cudaGetLastError();
+        }
+    }
     k_zrhs<R><<<grd, NT, sr, a.stream>>>(a, zchunk, tr);
     if (a.ev) cudaEventRecord(a.ev[3], a.stream);
     return cudaGetLastError();
