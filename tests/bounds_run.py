@@ -66,6 +66,7 @@ def main() -> int:
         run(f"fp32_o{order}_{dims}_cpasync", *dims, order, F32, env={"OSB_FP32_LOADS": "cpasync"})
     run("fp32_o10_split3", 24, 16, 12, 10, F32, env={"OSB_FP32_STAGE": "split3"})
     run("fp32_o4_zmarch", 72, 24, 16, 4, F32, env={"OSB_FP32_STAGE": "zmarch"})
+    run("fp32_o8_wide_residual", 104, 32, 20, 8, F32, env={"OSB_FP32_ZRHS": "wide"})
     run("fp64_o4_formB", 20, 12, 10, 4, visc=1)
     run("fp64_o4_euler", 20, 12, 10, 4, euler=True)
     run("fp32_o4_euler", 72, 24, 16, 4, F32, euler=True)

@@ -35,7 +35,7 @@ def test_bounds_check_build_reports_no_violation_on_any_path():
     state = np.array(out.pop("_state"))
     bad = {k: v for k, v in out.items() if v != 0}
     assert not bad, bad
-    assert len(out) == 61
+    assert len(out) == 62
     case = orc.Case(13, 11, 9, order=4, Re=300.0, dt=1e-3)
     Qo = orc.rk3_step(case, orc.tgv_init(case, inputs.gaussian_noise(13, 11, 9, seed=33), 1e-3), 3)
     for m in range(5):

@@ -322,6 +322,28 @@ def test_fp32_zmarch_agrees_with_three_kernel_stage(osb, order, monkeypatch):
         assert err < 2e-6, (m, err)
 
 
+@pytest.mark.parametrize("dims,order", [((36, 18, 20), 8), ((30, 14, 11), 8), ((72, 22, 9), 6), ((8, 6, 5), 6)])
+def test_fp32_narrow_residual_kernel_agrees_with_wide_one(osb, dims, order, monkeypatch):
+    """Orders 6 and 8 take the narrow residual kernel (32x4 tiles, z taps of
+    the flux and viscous sums scattered into pending sums); OSB_FP32_ZRHS=wide
+    the 32x8 one with register queues.  Same operator, other summation order:
+    the states after five steps differ by FP32 rounding only.  y extents not a
+    multiple of 4 (ragged narrow tiles), an x extent that is not a multiple of 4
+    (4-byte loads), and a grid smaller than the stencil are included."""
+    nx, ny, nz = dims
+    noise = inputs.gaussian_noise(nx, ny, nz, seed=15)
+    out = []
+    for mode in ("narrow", "wide"):
+        monkeypatch.setenv("OSB_FP32_ZRHS", mode)
+        g = _grid(osb, nx, ny, nz, order=order, precision=osb.OSB_FP32, dt=1e-3, Re=400.0)
+        g.init_taylor_green(noise, 1e-2)
+        g.step(5)
+        out.append(g.get_state())
+        assert g.diagnostics()["nonfinite"] == 0
+    for m, err in enumerate(_fp32_err(out[0], out[1])):
+        assert err < 2e-6, (m, err)
+
+
 @pytest.mark.parametrize("dims,order", [((40, 40, 40), 4), ((72, 20, 30), 4), ((37, 20, 9), 2), ((64, 24, 17), 2),
                                         ((70, 9, 33), 4), ((6, 5, 3), 4)])
 def test_fp32_fused_stage_agrees_with_two_and_three_kernel_stages(osb, dims, order, monkeypatch):
