@@ -310,10 +310,9 @@ def run_ensemble(torch, osb, inputs, steps, precision):
         g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
         grids.append(g)
     tuned = {}
-    if ensemble_launches(precision, len(specs))["mode"] == "persistent":  # tile depths of the persistent kernel
-        for g in grids:
-            if g.cfg.nx not in tuned:
-                tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
+    if ensemble_launches(precision, len(specs))["mode"] == "persistent":
+        # tile depths of the persistent kernel, tuned on the whole ensemble
+        tuned = {k[0]: v for k, v in osb.autotune_batch(grids, trial_steps=2).items()}
     pts = sum(g.cfg.n for g in grids)
     osb.batch_step(grids, 2)              # warm-up (kernels, step graphs)
     torch.cuda.synchronize()

@@ -253,6 +253,25 @@ osb_status osb_batch_configure(double wait_limit_seconds, int test_stall);
  * afterwards (through a host copy).  *best_tz receives the choice (may be NULL). */
 osb_status osb_autotune(osb_grid *grid, int trial_steps, int *best_tz);
 
+/* Tile depths for an ensemble, tuned in place: for each distinct grid shape
+ * in turn (largest total points first; the others held at their current
+ * depths), the candidate depths of osb_autotune are timed on
+ * osb_batch_step's persistent kernel over the whole ensemble, trial_steps
+ * steps each, and the fastest is kept in the process-wide table (and the
+ * $OSB_AUTOTUNE_CACHE file).  A grid timed alone favours short z chunks for
+ * parallelism; inside a large ensemble the others supply it, and longer
+ * chunks save the z-queue warm-up planes (64 grids of 32^3..128^3, FP32:
+ * 1.48e10 -> 1.65e10 point-stages/s).  The grids' states, times and step
+ * counts are restored afterwards (through host copies).  Requirements as
+ * osb_batch_step's; errors: OSB_ERR_INVALID_ARG (NULL grids, n outside
+ * 1..128, trial_steps < 1), and those of osb_batch_step. */
+osb_status osb_autotune_batch(osb_grid *const *grids, int n, int trial_steps);
+
+/* The z planes per work item that osb_batch_step's persistent kernel uses for
+ * grids of this descriptor's shape (the tuned depth, else the default: 8 for
+ * FP32, 4 otherwise).  0 for an invalid descriptor. */
+int osb_tile_depth(const osb_grid_desc *desc);
+
 /* Diagnostics of a caller-provided state without any device allocation and
  * without a grid object.  The state is read as a fully periodic box
  * [0, 2 pi)^3 (h = 2 pi / n, wrapped stencils); states of grids with symmetry

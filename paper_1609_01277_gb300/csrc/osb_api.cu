@@ -1464,6 +1464,110 @@ osb_status osb_autotune(osb_grid *g, int trial_steps, int *best_tz) {
     return OSB_OK;
 }
 
+int osb_tile_depth(const osb_grid_desc *desc) {
+    if (!desc_ok(desc)) return 0;
+    return tile_depth(*desc);
+}
+
+osb_status osb_autotune_batch(osb_grid *const *grids, int n, int trial_steps) {
+    if (!grids || n < 1 || n > MAXB || trial_steps < 1) return fail(OSB_ERR_INVALID_ARG, "invalid argument");
+    for (int i = 0; i < n; ++i)
+        if (!grids[i]) return fail(OSB_ERR_INVALID_ARG, "NULL grid in batch");
+    NvtxRange range("osb_autotune_batch");
+    // distinct shapes, largest total points first
+    std::map<std::string, long long> pts;
+    std::map<std::string, int> depth;
+    for (int i = 0; i < n; ++i) {
+        const std::string k = shape_key(grids[i]->desc);
+        pts[k] += (long long)grids[i]->d.n;
+        depth[k] = grids[i]->d.nz;
+    }
+    std::vector<std::pair<long long, std::string>> order;
+    for (auto &kv : pts) order.push_back({kv.second, kv.first});
+    std::sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    // the states to restore
+    struct Saved {
+        std::vector<double> q;
+        int cur;
+        double t;
+        long long step;
+    };
+    std::vector<Saved> saved(n);
+    for (int i = 0; i < n; ++i) {
+        osb_grid *g = grids[i];
+        try {
+            saved[i].q.resize(5 * (size_t)g->d.n);
+        } catch (...) {
+            return fail(OSB_ERR_INVALID_ARG, "host allocation failed");
+        }
+        saved[i].cur = g->cur;
+        saved[i].t = g->t;
+        saved[i].step = g->step;
+        osb_status s = osb_get_state(g, saved[i].q.data());
+        if (s != OSB_OK) return s;
+    }
+    const bool f32 = grids[0]->desc.precision == OSB_FP32;
+    const int cand64[] = {1, 2, 4, 8, 16}, cand32[] = {4, 8, 16, 32, 0};
+    const int *cand = f32 ? cand32 : cand64;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return fail(OSB_ERR_CUDA, "autotune: event create failed");
+    osb_status s = OSB_OK;
+    cudaStream_t st = grids[0]->st;
+    // coordinate descent: each shape's depth in turn, the others held, timed
+    // on the whole ensemble
+    for (auto &ok : order) {
+        const std::string &key = ok.second;
+        int best = -1;
+        float best_ms = 1e30f;
+        for (int ci = 0; ci < 5 && s == OSB_OK; ++ci) {
+            const int tz = cand[ci];
+            if (tz == 0 || (tz > depth[key] && tz != cand[0])) continue;
+            {
+                std::lock_guard<std::mutex> lock(g_tune_mu);
+                tune_load_locked();
+                (*g_tune)[key] = tz;
+            }
+            s = batch_run(grids, n, 1, BATCH_PERSISTENT);  // warm-up (captures the graph)
+            if (s != OSB_OK) break;
+            cudaEventRecord(e0, st);
+            s = batch_run(grids, n, trial_steps, BATCH_PERSISTENT);
+            cudaEventRecord(e1, st);
+            if (s != OSB_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = tz;
+            }
+        }
+        if (best > 0) {
+            std::lock_guard<std::mutex> lock(g_tune_mu);
+            (*g_tune)[key] = best;
+        }
+        if (s != OSB_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_save_locked();
+    }
+    osb_status r = OSB_OK;
+    for (int i = 0; i < n; ++i) {
+        osb_grid *g = grids[i];
+        g->cur = saved[i].cur;
+        g->qc = saved[i].cur;
+        const osb_status ri = osb_set_state(g, saved[i].q.data());
+        if (r == OSB_OK) r = ri;
+        g->t = saved[i].t;
+        g->step = saved[i].step;
+    }
+    if (s != OSB_OK) return s;
+    return r;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

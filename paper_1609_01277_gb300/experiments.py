@@ -241,12 +241,8 @@ def ensemble_run(steps: int, precisions=("fp64", "fp32"), every: int = 50, count
             grids.append(g)
         tuned = {}
         mode = os.environ.get("OSB_BATCH_MODE") or ("streams" if precision == "df64" else "persistent")
-        for g in grids if autotune and mode == "persistent" else []:  # tile depths of the persistent kernel
-            if g.cfg.nx not in tuned:
-                tuned[g.cfg.nx] = osb.autotune(g, trial_steps=2)
-        for i, g in enumerate(grids):  # autotuning stepped the grids: start again
-            n = g.cfg.nx
-            g.init_taylor_green(torch.from_numpy(inputs.gaussian_noise(n, n, n, 1000 + i)).cuda(), 1e-4)
+        if autotune and mode == "persistent":  # tile depths of the persistent kernel, tuned on the ensemble
+            tuned = {k[0]: v for k, v in osb.autotune_batch(grids, trial_steps=2).items()}
         ke = [[g.diagnostics()["ke"] for g in grids]]
         seconds, done = 0.0, 0
         while done < steps:

@@ -29,7 +29,8 @@ EXPORTS = ("osb_state_bytes", "osb_workspace_bytes", "osb_grid_create", "osb_gri
            "osb_init_taylor_green", "osb_set_state", "osb_get_state", "osb_set_state_device",
            "osb_euler_step",
            "osb_get_state_device", "osb_residual", "osb_rk3_step", "osb_diagnostics",
-           "osb_batch_step", "osb_batch_configure", "osb_autotune", "osb_diagnostics_noalloc",
+           "osb_batch_step", "osb_batch_configure", "osb_autotune", "osb_autotune_batch", "osb_tile_depth",
+           "osb_diagnostics_noalloc",
            "osb_closure_param_count", "osb_closure_workspace_bytes", "osb_closure_create", "osb_closure_destroy",
            "osb_closure_set_normalization", "osb_closure_set_channels", "osb_closure_set_dissipative", "osb_closure_set_loss_weight", "osb_closure_status", "osb_closure_sync_weights",
            "osb_closure_forward", "osb_closure_loss_grad", "osb_closure_adam_step", "osb_grid_set_closure",
@@ -94,6 +95,9 @@ def load(path: str | None = None):
     L.osb_batch_step.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
     L.osb_batch_configure.argtypes = [ctypes.c_double, ctypes.c_int]
     L.osb_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.osb_autotune_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int]
+    L.osb_tile_depth.argtypes = [ctypes.c_void_p]
+    L.osb_tile_depth.restype = ctypes.c_int
     L.osb_diagnostics_noalloc.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, vp, vp]
     L.osb_scalar_rk3.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_int, vp]
@@ -363,6 +367,24 @@ def autotune(grid: "Grid", trial_steps: int = 3) -> int:
     tz = ctypes.c_int(0)
     check(load().osb_autotune(grid.handle, int(trial_steps), ctypes.byref(tz)), "osb_autotune")
     return tz.value
+
+
+def autotune_batch(grids, trial_steps: int = 2) -> dict:
+    """Tune the persistent kernel's tile depth of every grid shape in the
+    ensemble, timed on the whole ensemble (states restored); returns
+    {shape: depth}."""
+    arr = (ctypes.c_void_p * len(grids))(*[g.handle for g in grids])
+    check(load().osb_autotune_batch(arr, len(grids), int(trial_steps)), "osb_autotune_batch")
+    out = {}
+    for g in grids:
+        out[(g.cfg.nx, g.cfg.ny, g.cfg.nz)] = tile_depth(g.cfg)
+    return out
+
+
+def tile_depth(cfg: "Config") -> int:
+    """Tile depth (z planes per work item) the ensemble kernel uses for this shape."""
+    d = cfg.desc() if hasattr(cfg, "desc") else cfg
+    return int(load().osb_tile_depth(ctypes.byref(d)))
 
 
 def fp64_rate(blocks: int = 152 * 8, iters: int = 2000, repeats: int = 5) -> dict:

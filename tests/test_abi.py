@@ -168,6 +168,17 @@ def test_scalar_rejects_bad_arguments_before_gpu_work(osb):
 
 
 
+def test_batch_autotune_and_tile_depth_reject_bad_arguments_before_gpu_work(osb):
+    L = osb.load()
+    assert L.osb_autotune_batch(None, 1, 2) == 1
+    assert L.osb_tile_depth(None) == 0
+    bad = osb.GridDesc(8, 8, 8, 5, osb.OSB_FP64, 0)
+    assert L.osb_tile_depth(ctypes.byref(bad)) == 0
+    d32 = osb.GridDesc(40, 40, 40, 4, osb.OSB_FP32, 0)
+    d64 = osb.GridDesc(40, 40, 40, 4, osb.OSB_FP64, 0)
+    assert L.osb_tile_depth(ctypes.byref(d32)) >= 1 and L.osb_tile_depth(ctypes.byref(d64)) >= 1
+
+
 def test_z_slab_calls_reject_null_grids(osb):
     L = osb.load()
     assert L.osb_set_z_slab(None, 64) == 1

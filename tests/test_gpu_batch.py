@@ -304,3 +304,22 @@ def test_batch_stream_mode_more_grids_than_streams(osb, monkeypatch):
     for ga, gb in zip(a, b):
         assert np.array_equal(ga.get_state(), gb.get_state())
 
+
+def test_batch_autotune_restores_states_and_sets_depths(osb):
+    """The in-ensemble tuner times candidate depths on the whole ensemble and
+    restores every grid: stepping afterwards equals stepping untouched grids,
+    and every shape's depth is one of the candidates."""
+    specs = [(16, 1600.0, 0.1, 2e-3), (24, 400.0, 0.2, 1.5e-3), (16, 800.0, 0.15, 2e-3), (32, 100.0, 0.3, 1e-3)]
+    for prec, cands in ((osb.OSB_FP32, {4, 8, 16, 32}), (osb.OSB_FP64, {1, 2, 4, 8, 16})):
+        a = _ensemble(osb, specs, prec, seed=50)
+        b = _ensemble(osb, specs, prec, seed=50)
+        depths = osb.autotune_batch(b, trial_steps=1)
+        assert set(depths) == {(16, 16, 16), (24, 24, 24), (32, 32, 32)}
+        assert all(v in cands for v in depths.values()), depths
+        for g in b:
+            assert g.diagnostics()["step"] == 0
+        osb.batch_step(a, 3)
+        osb.batch_step(b, 3)
+        for ga, gb in zip(a, b):
+            assert np.array_equal(ga.get_state(), gb.get_state())
+
