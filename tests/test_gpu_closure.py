@@ -152,6 +152,30 @@ def test_attached_closure_adds_correction_to_residual(mods):
     assert np.array_equal(p.get_state(), q.get_state())
 
 
+def test_closure_in_fp32_order8_steps_narrow_and_wide_residual_kernels(mods, monkeypatch):
+    """FP32 order-8 steps add the closure inside the z-march residual kernels
+    (narrow by default, the 32x8 one with OSB_FP32_ZRHS=wide): the two agree
+    to FP32 rounding, and both differ from the plain step by far more."""
+    osb, closure, torch = mods
+    n = 32
+    c, *_ = _setup(mods, n=(n, n, n), seed=29)
+    noise = inputs.gaussian_noise(n, n, n, 3)
+    out = {}
+    for mode, attach in (("narrow", True), ("wide", True), ("narrow", False)):
+        monkeypatch.setenv("OSB_FP32_ZRHS", mode)
+        g = osb.Grid(osb.Config(n, n, n, order=8, precision=osb.OSB_FP32, dt=1e-3))
+        g.init_taylor_green(noise, 1e-2)
+        if attach:
+            c.attach(g)
+        g.step(2)
+        out[(mode, attach)] = g.get_state()
+    a, b, plain = out[("narrow", True)], out[("wide", True)], out[("narrow", False)]
+    scale = np.linalg.norm((a - plain).ravel())
+    assert scale > 1e-8 * np.linalg.norm(plain.ravel())
+    assert np.linalg.norm((a - b).ravel()) < 1e-3 * scale
+    c.status()
+
+
 def test_training_reduces_a_priori_error(mods):
     """Closure data from the solver (fine 64^3 -> coarse 16^3, factor 4): after
     training, the closure explains part of the commutation residual on held-out
